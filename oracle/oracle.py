@@ -1,0 +1,133 @@
+"""ctypes shim over the FP64 CPU oracle in rf_oracle.c.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check of
+__graft_entry__ and by the CPU-baseline leg of bench.py, never by the product
+package.  It shares no code with the CUDA library.
+
+Functions follow the paper (Farina et al., Sec. 3 and Appendix A): see the
+header of rf_oracle.c for the step-by-step description and the pins.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rf_oracle.c")
+_LIB = os.path.join(_HERE, "librforacle.so")
+
+NORM_GAUSS_PEAK = 0
+NORM_UNIT_SUM = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile rf_oracle.c with gcc (no FMA contraction) into librforacle.so."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off",
+                           "-fno-fast-math", "-fPIC", "-shared", _SRC,
+                           "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        d, i, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+        vp = ctypes.c_void_p
+        lib.orc_rf3_coeffs.argtypes = [d, i, vp, vp, vp]
+        lib.orc_rf3_coeffs.restype = None
+        lib.orc_rf1_coeffs.argtypes = [d, i, i, vp, vp]
+        lib.orc_rf1_coeffs.restype = None
+        lib.orc_line.argtypes = [i, i, i, d, i, i64, vp, vp, vp, vp]
+        lib.orc_line.restype = i
+        lib.orc_vh.argtypes = [i, i, i, d, i, i64, i64, i64, i64, vp, i64,
+                               vp, vp, i64, vp, vp]
+        lib.orc_vh.restype = i
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def rf3_coeffs(sigma: float, norm: int = NORM_GAUSS_PEAK):
+    """Theorem 3.1 coefficients: returns (a[4], alpha[3], beta)."""
+    lib = _load()
+    a = np.zeros(4)
+    al = np.zeros(3)
+    b = np.zeros(1)
+    lib.orc_rf3_coeffs(float(sigma), int(norm), _ptr(a), _ptr(al), _ptr(b))
+    return a, al, float(b[0])
+
+
+def rf1_coeffs(sigma: float, K: int, norm: int = NORM_GAUSS_PEAK):
+    """1st-RF coefficients from Hayden's relation: returns (alpha, beta)."""
+    lib = _load()
+    al = np.zeros(1)
+    b = np.zeros(1)
+    lib.orc_rf1_coeffs(float(sigma), int(K), int(norm), _ptr(al), _ptr(b))
+    return float(al[0]), float(b[0])
+
+
+def line(x, sigma, mask=None, *, order: int = 3, iters: int = 1,
+         adjoint: bool = False, img_factor: float = 3.0,
+         norm: int = NORM_GAUSS_PEAK) -> np.ndarray:
+    """Apply one 1-D filter G (or G^T) to the line x."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    sig = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma, np.float64), (n,)))
+    m = (np.ones(n, np.uint8) if mask is None
+         else np.ascontiguousarray(mask, dtype=np.uint8))
+    out = np.zeros(n)
+    rc = lib.orc_line(order, iters, int(adjoint), float(img_factor), norm, n,
+                      _ptr(m), _ptr(sig), _ptr(x), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_line failed with code {rc}")
+    return out
+
+
+def vh(field, mask, Lx, Ly, *, order: int = 3, iters: int = 1,
+       adjoint: bool = False, img_factor: float = 3.0,
+       norm: int = NORM_GAUSS_PEAK) -> np.ndarray:
+    """V_H = G_y G_x (adjoint: G_x^T G_y^T) on a field [nvar][nz][ny][nx].
+
+    field may also be [nz][ny][nx] or [ny][nx]; mask is [mask_nz][ny][nx]
+    or [ny][nx]; Lx, Ly are [L_nz][ny][nx] or [ny][nx] (grid units).
+    """
+    lib = _load()
+    f = np.asarray(field, dtype=np.float64)
+    shape = f.shape
+    while f.ndim < 4:
+        f = f[None]
+    nvar, nz, ny, nx = f.shape
+    f = np.ascontiguousarray(f)
+
+    def lev(a, dtype):
+        a = np.asarray(a, dtype=dtype)
+        if a.ndim == 2:
+            a = a[None]
+        return np.ascontiguousarray(a)
+
+    m = lev(mask, np.uint8)
+    lx = lev(Lx, np.float64)
+    ly = lev(Ly, np.float64)
+    out = np.zeros_like(f)
+    rc = lib.orc_vh(order, iters, int(adjoint), float(img_factor), norm,
+                    nx, ny, nz, nvar, _ptr(m), m.shape[0], _ptr(lx), _ptr(ly),
+                    lx.shape[0], _ptr(f), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_vh failed with code {rc}")
+    return out.reshape(shape)

@@ -1,0 +1,406 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the
+constants printed in Appendix A, closed forms derived from the transfer
+function, dense triangular-solve matrices, invariants and exact identities.
+"""
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import polynomial as npoly
+from scipy.linalg import solve_triangular
+
+from oracle import oracle as orc
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+
+
+def paper_constants():
+    out = {}
+    with open(GOLD) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, value = line.split()[:2]
+            out[name] = float(value)
+    return out
+
+
+C = paper_constants()
+
+
+# ---------------------------------------------------------------- Appendix A
+def test_abramowitz_stegun_approximation_bound():
+    """The rational approximation of the Gaussian (Appendix A) is within the
+    printed bound of exp(-t^2/2)/sqrt(2 pi)."""
+    t = np.linspace(-8, 8, 20001)
+    approx = 1.0 / (C["as_b0"] + C["as_b2"] * t**2 + C["as_b4"] * t**4
+                    + C["as_b6"] * t**6)
+    exact = np.exp(-t**2 / 2) / np.sqrt(2 * np.pi)
+    assert np.max(np.abs(approx - exact)) < C["as_err_bound"]
+
+
+def test_newton_root_and_factorisation():
+    """s = 1.16680481/sigma is a root of b0 - b2 u^2 + b4 u^4 - b6 u^6 and the
+    printed causal/anticausal factors multiply back to that polynomial."""
+    b0, b2, b4, b6 = C["as_b0"], C["as_b2"], C["as_b4"], C["as_b6"]
+    poly = np.array([b0, 0, -b2, 0, b4, 0, -b6])          # ascending in u
+    x = C["newton_root"]
+    assert abs(npoly.polyval(x, poly)) < 1e-6 * b0
+    fr, q0, q1 = C["factor_real"], C["factor_quad_c0"], C["factor_quad_c1"]
+    causal = npoly.polymul([fr, 1.0], [q0, q1, 1.0])
+    anticausal = npoly.polymul([fr, -1.0], [q0, -q1, 1.0])
+    prod = npoly.polymul(causal, anticausal)
+    np.testing.assert_allclose(prod, poly / b6, rtol=0, atol=2e-5 * abs(b0 / b6))
+    # the causal factor is the Theorem's cubic: P0 + P1 u + P2 u^2 + u^3
+    np.testing.assert_allclose(
+        causal, [C["theorem_P0"], C["theorem_P1"], C["theorem_P2"], 1.0],
+        rtol=5e-7)
+    assert C["theorem_a1_quad"] == pytest.approx(2 * C["theorem_P2"], abs=1e-6)
+
+
+@pytest.mark.parametrize("sigma", [0.3, 1.0, 2.0, 7.5, 10.0, 40.0, 123.0])
+def test_theorem_coefficients_from_z_transform(sigma):
+    """a_{i,0..3} are the coefficients of D(sigma (1 - z^-1)), D being the
+    product of the printed causal factors (backward difference s = 1 - z^-1)."""
+    fr, q0, q1 = C["factor_real"], C["factor_quad_c0"], C["factor_quad_c1"]
+    D = npoly.polymul([fr, 1.0], [q0, q1, 1.0])
+    u = np.array([sigma, -sigma])                       # u(w) = sigma - sigma w
+    acc = np.zeros(1)
+    upow = np.array([1.0])
+    for c in D:
+        acc = npoly.polyadd(acc, c * upow)
+        upow = npoly.polymul(upow, u)
+    expect = np.array([acc[0], -acc[1], -acc[2], -acc[3]])
+    a, alpha, beta = orc.rf3_coeffs(sigma)
+    np.testing.assert_allclose(a, expect, rtol=2e-6, atol=2e-6 * abs(expect[0]))
+    np.testing.assert_allclose(alpha, a[1:] / a[0], rtol=1e-15)
+    # normalisation: beta = (2 pi sigma^2)^(1/4) (a0 - a1 - a2 - a3)/a0
+    g = (2 * np.pi * sigma**2) ** 0.25
+    assert beta == pytest.approx(g * C["theorem_P0"] / a[0], rel=1e-9)
+
+
+# ------------------------------------------------------------- closed forms
+def impulse_line(sigma, **kw):
+    n = int(60 * sigma) + 64
+    x = np.zeros(2 * n + 1)
+    x[n] = 1.0
+    return np.arange(2 * n + 1) - n, orc.line(x, sigma, img_factor=0.0, **kw)
+
+
+@pytest.mark.parametrize("sigma", [2.0, 10.0, 40.0])
+def test_rf3_dc_gain_is_sqrt_2pi_sigma(sigma):
+    """Each pass has DC gain (2 pi sigma^2)^(1/4) (Appendix A normalisation),
+    so forward + backward sum to sqrt(2 pi) sigma: the sum of exp(-x^2/2s^2)."""
+    _, h = impulse_line(sigma)
+    assert h.sum() == pytest.approx(np.sqrt(2 * np.pi) * sigma, rel=1e-12)
+
+
+@pytest.mark.parametrize("sigma", [2.0, 10.0, 40.0])
+def test_rf3_impulse_variance_closed_form(sigma):
+    """Cumulant expansion of 1/D(sigma(1-e^t)) times its mirror gives
+    Var = 2[(P1/P0) sigma + ((P1/P0)^2 - 2 P2/P0) sigma^2], mean 0."""
+    n, h = impulse_line(sigma)
+    P0, P1, P2 = C["theorem_P0"], C["theorem_P1"], C["theorem_P2"]
+    m0 = h.sum()
+    mean = (n * h).sum() / m0
+    var = ((n - mean) ** 2 * h).sum() / m0
+    r = P1 / P0
+    assert abs(mean) < 1e-9 * sigma
+    assert var == pytest.approx(2 * (r * sigma + (r * r - 2 * P2 / P0) * sigma**2),
+                                rel=1e-9)
+
+
+@pytest.mark.parametrize("sigma,K", [(2.0, 1), (4.0, 5), (10.0, 5), (10.0, 10)])
+def test_rf1_hayden_variance_and_gain(sigma, K):
+    """Hayden's relation R^2 = 2K alpha/(1-alpha)^2 dx^2 makes the K-times
+    iterated forward+backward impulse response have variance sigma^2; the
+    unit-sum form has gain 1, the Gaussian-peak form sqrt(2 pi) sigma."""
+    n, h = impulse_line(sigma, order=1, iters=K, norm=orc.NORM_UNIT_SUM)
+    assert h.sum() == pytest.approx(1.0, rel=1e-11)
+    assert ((n * n) * h).sum() == pytest.approx(sigma**2, rel=1e-9)
+    _, hg = impulse_line(sigma, order=1, iters=K)
+    assert hg.sum() == pytest.approx(np.sqrt(2 * np.pi) * sigma, rel=1e-11)
+
+
+def test_rf1_coefficients_satisfy_hayden():
+    for sigma, K in [(1.5, 1), (5.0, 5), (40.0, 10)]:
+        alpha, beta = orc.rf1_coeffs(sigma, K, orc.NORM_UNIT_SUM)
+        assert 0 < alpha < 1
+        assert beta == pytest.approx(1 - alpha, rel=1e-13)
+        assert 2 * K * alpha / (1 - alpha) ** 2 == pytest.approx(sigma**2, rel=1e-11)
+
+
+# ------------------------------------------------------------- dense matrices
+def dense_pair_matrix(sig, order, K, norm):
+    """One forward+backward pair U^-1 D L^-1 D on an all-sea extended
+    segment, from triangular solves (L unit lower with L[i,i-j] = -alpha_{i,j},
+    U unit upper with U[i,i+j] = -alpha_{i,j}, D = diag(beta)); the 1st-RF
+    coefficients are those for K iterations."""
+    m = len(sig)
+    Lm = np.eye(m)
+    Um = np.eye(m)
+    beta = np.zeros(m)
+    for i, s in enumerate(sig):
+        if order == 3:
+            _, al, beta[i] = orc.rf3_coeffs(s, norm)
+        else:
+            a1, beta[i] = orc.rf1_coeffs(s, K, norm)
+            al = [a1]
+        for j, a in enumerate(al, start=1):
+            if i - j >= 0:
+                Lm[i, i - j] = -a
+            if i + j < m:
+                Um[i, i + j] = -a
+    D = np.diag(beta)
+    return solve_triangular(Um, D @ solve_triangular(Lm, D, lower=True), lower=False)
+
+
+def dense_line_matrix(mask, sig, order=3, K=1, img=3.0, norm=0):
+    """The whole line operator as a dense matrix, segment by segment: extend
+    each sea run by ceil(img*sigma_coast) points with the coastal sigma,
+    apply the pair, restrict back; K iterations give (R G E)^K."""
+    n = len(mask)
+    G = np.zeros((n, n))
+    i = 0
+    while i < n:
+        if not mask[i]:
+            i += 1
+            continue
+        b = i
+        while i < n and mask[i]:
+            i += 1
+        seg = list(range(b, i))
+        nl = int(np.ceil(img * sig[b])) if img > 0 else 0
+        nr = int(np.ceil(img * sig[i - 1])) if img > 0 else 0
+        ext = [sig[b]] * nl + [sig[t] for t in seg] + [sig[i - 1]] * nr
+        L = len(seg)
+        R = np.zeros((L, len(ext)))
+        R[np.arange(L), nl + np.arange(L)] = 1.0
+        blk = R @ dense_pair_matrix(ext, order, K, norm) @ R.T
+        G[np.ix_(seg, seg)] = np.linalg.matrix_power(blk, K)
+    return G
+
+
+def oracle_line_matrix(mask, sig, adjoint=False, **kw):
+    n = len(mask)
+    cols = []
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        cols.append(orc.line(e, sig, mask, adjoint=adjoint, **kw))
+    return np.array(cols).T
+
+
+@pytest.mark.parametrize("img", [0.0, 1.0, 2.5])
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 1), (1, 5)])
+def test_line_matches_dense_triangular_solves(order, K, img):
+    rng = np.random.default_rng(7)
+    n = 23
+    mask = np.ones(n, np.uint8)
+    mask[[0, 6, 7, 15]] = 0
+    sig = rng.uniform(0.6, 3.0, n)
+    G = dense_line_matrix(mask, sig, order, K, img)
+    O = oracle_line_matrix(mask, sig, order=order, iters=K, img_factor=img)
+    np.testing.assert_allclose(O, G, rtol=0, atol=1e-12 * np.abs(G).max())
+    OT = oracle_line_matrix(mask, sig, adjoint=True, order=order, iters=K,
+                            img_factor=img)
+    np.testing.assert_allclose(OT, G.T, rtol=0, atol=1e-12 * np.abs(G).max())
+
+
+def test_heuristic_initial_conditions_printed_form():
+    """With no imaginary points, the first three forward outputs and the last
+    three backward outputs follow the printed initial conditions (Sec. 3.1)."""
+    rng = np.random.default_rng(3)
+    n = 9
+    sig = rng.uniform(1.0, 4.0, n)
+    x = rng.standard_normal(n)
+    al = np.zeros((n, 3))
+    be = np.zeros(n)
+    for i in range(n):
+        _, al[i], be[i] = orc.rf3_coeffs(sig[i])
+    p = np.zeros(n)
+    p[0] = be[0] * x[0]
+    p[1] = be[1] * x[1] + al[1, 0] * p[0]
+    p[2] = be[2] * x[2] + al[2, 0] * p[1] + al[2, 1] * p[0]
+    for i in range(3, n):
+        p[i] = be[i] * x[i] + al[i, 0] * p[i - 1] + al[i, 1] * p[i - 2] + al[i, 2] * p[i - 3]
+    s = np.zeros(n)
+    s[n - 1] = be[n - 1] * p[n - 1]
+    s[n - 2] = be[n - 2] * p[n - 2] + al[n - 2, 0] * s[n - 1]
+    s[n - 3] = be[n - 3] * p[n - 3] + al[n - 3, 0] * s[n - 2] + al[n - 3, 1] * s[n - 1]
+    for i in range(n - 4, -1, -1):
+        s[i] = be[i] * p[i] + al[i, 0] * s[i + 1] + al[i, 1] * s[i + 2] + al[i, 2] * s[i + 3]
+    np.testing.assert_allclose(orc.line(x, sig, img_factor=0.0), s, rtol=1e-13,
+                               atol=1e-14)
+
+
+# ---------------------------------------------------------------- coasts
+def test_single_point_segment_gives_beta_squared():
+    mask = np.array([0, 1, 0], np.uint8)
+    x = np.array([5.0, 2.0, 7.0])
+    _, _, beta = orc.rf3_coeffs(3.0)
+    y = orc.line(x, 3.0, mask, img_factor=0.0)
+    assert y[0] == 0.0 and y[2] == 0.0
+    assert y[1] == pytest.approx(beta * beta * 2.0, rel=1e-14)
+
+
+def test_imaginary_points_equal_zero_padded_sea():
+    """A segment extended by imaginary points behaves exactly as the same
+    segment inside a longer all-sea line padded with zero input and the
+    coastal length scale, restricted back to the segment."""
+    rng = np.random.default_rng(11)
+    L = 40
+    sig = rng.uniform(2.0, 6.0, L)
+    x = rng.standard_normal(L)
+    f = 2.0
+    nl = int(np.ceil(f * sig[0]))
+    nr = int(np.ceil(f * sig[-1]))
+    pad_sig = np.concatenate([[sig[0]] * nl, sig, [sig[-1]] * nr])
+    # 3rd-RF: one pass pair over the padded line, read back on the segment
+    y = orc.line(x, sig, img_factor=f)
+    pad_x = np.concatenate([np.zeros(nl), x, np.zeros(nr)])
+    ref = orc.line(pad_x, pad_sig, img_factor=0.0)[nl:nl + L]
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-13)
+    # 1st-RF x5: every iteration re-pads with zeros (no carried imaginary values)
+    G = dense_line_matrix(np.ones(L, np.uint8), sig, 1, 5, f)
+    y1 = orc.line(x, sig, img_factor=f, order=1, iters=5)
+    np.testing.assert_allclose(y1, G @ x, rtol=1e-12, atol=1e-13)
+
+
+def test_land_isolates_signal():
+    """An impulse on one side of a one-cell land strip gives exactly zero on
+    the other side, in 1-D and behind a full land wall in 2-D."""
+    n = 60
+    mask = np.ones(n, np.uint8)
+    mask[30] = 0
+    x = np.zeros(n)
+    x[25] = 1.0
+    for order, K in [(3, 1), (1, 5)]:
+        y = orc.line(x, 8.0, mask, order=order, iters=K)
+        assert np.all(y[30:] == 0.0)
+        assert np.all(y[:30] != 0.0)
+    ny, nx = 24, 32
+    m2 = np.ones((ny, nx), np.uint8)
+    m2[:, 16] = 0
+    f = np.zeros((ny, nx))
+    f[12, 8] = 1.0
+    L = np.full((ny, nx), 5.0)
+    for order, K in [(3, 1), (1, 5)]:
+        for adj in (False, True):
+            out = orc.vh(f, m2, L, L, order=order, iters=K, adjoint=adj)
+            assert np.all(out[:, 16:] == 0.0)
+
+
+# ---------------------------------------------------------------- 2-D
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 5)])
+def test_constant_field_is_scaled_by_2pi_sx_sy(order, K):
+    """Away from the boundaries a constant c maps to c * 2 pi sigma_x sigma_y
+    (Gaussian-peak normalisation), and to c with the unit-sum form."""
+    ny, nx = 200, 220
+    sx, sy = 4.0, 3.0
+    m = np.ones((ny, nx), np.uint8)
+    f = np.full((ny, nx), 1.7)
+    out = orc.vh(f, m, np.full((ny, nx), sx), np.full((ny, nx), sy),
+                 order=order, iters=K, img_factor=0.0)
+    interior = out[90:110, 100:120]
+    np.testing.assert_allclose(interior, 1.7 * 2 * np.pi * sx * sy, rtol=1e-10)
+    out1 = orc.vh(f, m, np.full((ny, nx), sx), np.full((ny, nx), sy),
+                  order=order, iters=K, img_factor=0.0, norm=orc.NORM_UNIT_SUM)
+    np.testing.assert_allclose(out1[90:110, 100:120], 1.7, rtol=1e-10)
+
+
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 5)])
+def test_vh_equals_kronecker_of_line_matrices(order, K):
+    """V_H = G_y G_x on a tiny grid with land and varying sigma equals the
+    product of the block-diagonal row operator and column operator."""
+    rng = np.random.default_rng(5)
+    ny, nx = 9, 11
+    mask = (rng.uniform(size=(ny, nx)) > 0.25).astype(np.uint8)
+    Lx = rng.uniform(0.8, 3.0, (ny, nx))
+    Ly = rng.uniform(0.8, 3.0, (ny, nx))
+    N = nx * ny
+    Gx = np.zeros((N, N))
+    for j in range(ny):
+        idx = j * nx + np.arange(nx)
+        Gx[np.ix_(idx, idx)] = dense_line_matrix(mask[j], Lx[j], order, K, 1.5)
+    Gy = np.zeros((N, N))
+    for i in range(nx):
+        idx = np.arange(ny) * nx + i
+        Gy[np.ix_(idx, idx)] = dense_line_matrix(mask[:, i], Ly[:, i], order, K, 1.5)
+    V = Gy @ Gx
+    x = rng.standard_normal((ny, nx))
+    y = orc.vh(x, mask, Lx, Ly, order=order, iters=K, img_factor=1.5)
+    np.testing.assert_allclose(y.ravel(), V @ x.ravel(), rtol=0,
+                               atol=1e-12 * np.abs(V @ x.ravel()).max())
+    yt = orc.vh(x, mask, Lx, Ly, order=order, iters=K, img_factor=1.5, adjoint=True)
+    np.testing.assert_allclose(yt.ravel(), V.T @ x.ravel(), rtol=0,
+                               atol=1e-12 * np.abs(V.T @ x.ravel()).max())
+
+
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 5)])
+def test_adjoint_dot_product(order, K):
+    """<V x, y> = <x, V^T y> to 1e-12 on a multi-level field with land."""
+    rng = np.random.default_rng(9)
+    nz, ny, nx = 3, 40, 56
+    mask = (rng.uniform(size=(nz, ny, nx)) > 0.2).astype(np.uint8)
+    Lx = rng.uniform(2.0, 12.0, (ny, nx))
+    Ly = rng.uniform(2.0, 12.0, (ny, nx))
+    x = rng.standard_normal((2, nz, ny, nx))
+    y = rng.standard_normal((2, nz, ny, nx))
+    Vx = orc.vh(x, mask, Lx, Ly, order=order, iters=K)
+    VTy = orc.vh(y, mask, Lx, Ly, order=order, iters=K, adjoint=True)
+    lhs = np.vdot(Vx, y)
+    rhs = np.vdot(x, VTy)
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Vx) * np.linalg.norm(y)
+
+
+def test_uniform_sigma_all_sea_is_self_adjoint():
+    rng = np.random.default_rng(1)
+    ny, nx = 30, 34
+    m = np.ones((ny, nx), np.uint8)
+    L = np.full((ny, nx), 4.0)
+    x = rng.standard_normal((ny, nx))
+    a = orc.vh(x, m, L, L)
+    b = orc.vh(x, m, L, L, adjoint=True)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------- Remark 1
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 5)])
+def test_remark1_valid_bounds(order, K):
+    """Remark 1 in the two forms that hold for a discrete convolution:
+    pointwise |s - s*| <= ||eps_h||_2 ||s0||_2 (the Cauchy-Schwarz step of its
+    proof) and ||eps_s||_2 <= ||eps_h||_1 ||s0||_2 (Young)."""
+    sigma = 4.0
+    n = 1200
+    rng = np.random.default_rng(2)
+    s0 = np.zeros(n)
+    s0[400:800] = rng.standard_normal(400)
+    s = orc.line(s0, sigma, img_factor=0.0, order=order, iters=K)
+    k = np.arange(-300, 301)
+    g = np.exp(-k**2 / (2 * sigma**2))
+    s_star = np.convolve(s0, g, mode="same")
+    imp = np.zeros(n)
+    imp[600] = 1.0
+    h = orc.line(imp, sigma, img_factor=0.0, order=order, iters=K)[300:901]
+    eps_h = g - h
+    bound_pt = np.linalg.norm(eps_h) * np.linalg.norm(s0)
+    err = s - s_star
+    assert np.max(np.abs(err)) <= bound_pt
+    assert np.linalg.norm(err) <= np.abs(eps_h).sum() * np.linalg.norm(s0)
+
+
+# ------------------------------------------------------------- validation
+def test_invalid_inputs_rejected():
+    with pytest.raises(ValueError):
+        orc.line(np.ones(5), -1.0)
+    with pytest.raises(ValueError):
+        orc.line(np.ones(5), np.nan)
+    with pytest.raises(ValueError):
+        orc.line(np.ones(5), 2.0, order=3, iters=2)
+    # land points may carry any length scale
+    mask = np.array([1, 0, 1, 1, 0], np.uint8)
+    sig = np.array([2.0, -5.0, 2.0, 3.0, np.nan])
+    orc.line(np.ones(5), sig, mask)
