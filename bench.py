@@ -1,0 +1,353 @@
+"""Benchmark of the V_H recursive-filter operator on GB300.
+
+Workload: the regional-basin grid 1024 x 384 x 72 levels with two variables
+(T and S), ~30 % land with coastlines, length scales smooth in [5, 40] grid
+points (seeded synthetic stand-in for the Mediterranean configuration of the
+paper, Sec. 4).  One step = one 3rd-RF forward application V_H x and one
+adjoint application V_H^T y over the whole batch (56.6 M grid points each).
+Metric: grid points through one V_H application per second (forward and
+adjoint each count), i.e. 2 * points / step time.  The 1st-RF x5 filter is
+timed the same way for the speed-up.  Each field (226 MB per variable, 453 MB
+per step input) is larger than the 126 MB L2, so no L2 flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own batch (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpts/s of V_h 3rd-RF fwd+adjoint vs 1st-RF x5; % of HBM roofline"
+WORKLOAD = "regional basin 1024x384x72, T+S, 30% land, L in [5,40] (fwd+adjoint)"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--cpu-seconds", type=float, default=10.0,
+                   help="bound on the CPU oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1404_5756_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("source_hash") == source_hash():
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]),
+                                 hw=f[5], hwt=f[6], swt=f[7], pcap=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        loaded = [r for r in rows if r["power"] > 200.0] or rows
+        reasons = set()
+        for r in loaded:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r["sm"] for r in loaded])),
+                "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def make_inputs(nvar_override=None):
+    from paper_1404_5756_gb300 import synth
+    return synth.workload(2, nvar=nvar_override)
+
+
+def cpu_oracle_sample(w, seconds: float, order=3, iters=1):
+    """Time the FP64 oracle (single thread) on whole level slices of the same
+    workload, forward + adjoint per slice, until `seconds` have elapsed."""
+    from oracle import oracle
+    mask = w["mask"]
+    L = w["Lx"].astype(np.float64)
+    x = w["x"]
+    nslices = x.shape[0] * x.shape[1]
+    done, t0 = 0, time.perf_counter()
+    while True:
+        v, k = divmod(done % nslices, x.shape[1])
+        s = x[v, k].astype(np.float64)
+        y = oracle.vh(s, mask, L, L, order=order, iters=iters)
+        oracle.vh(y, mask, L, L, order=order, iters=iters, adjoint=True)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    pts = done * mask.size
+    return dict(value=2 * pts / el / 1e9, unit="Gpts/s", cores=1, kind="oracle",
+                sample=f"{done} level slices of {w['nx']}x{w['ny']} (fwd+adjoint each), "
+                       f"FP64 oracle, 1 thread, {el:.1f} s")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = make_inputs()
+    npts = w["nvar"] * w["nz"] * w["nx"] * w["ny"]
+    per_step = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, 0.0)
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(w, max(args.cpu_seconds / max(args.steps, 1), 0.0))
+        per_step.append(r)
+    val = float(np.mean([r["value"] for r in per_step]))
+    sample = per_step[-1]["sample"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Gpts/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 2 * npts / (val * 1e9) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": w["nx"], "ny": w["ny"], "nz": w["nz"],
+                   "nvar": w["nvar"]},
+        "cpu_baseline": {"value": val, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def timed_loop(torch, plan, x, y, z, steps, warmup, stream, events=True):
+    """Warm up, then time `steps` fwd+adjoint steps with CUDA events on the
+    launching stream; also per-application events for the roofline."""
+    for _ in range(warmup):
+        plan.apply(x, out=y)
+        plan.apply_adjoint(y, out=z)
+    torch.cuda.synchronize()
+    launches0 = plan.info()[3]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        plan.apply(x, out=y)
+        e1.record(stream)
+        plan.apply_adjoint(y, out=z)
+        e2.record(stream)
+    stop.record(stream)
+    stop.synchronize()
+    total_ms = start.elapsed_time(stop)
+    fwd = [a.elapsed_time(b) for a, b, _ in ev]
+    adj = [b.elapsed_time(c) for _, b, c in ev]
+    return total_ms, fwd, adj, plan.info()[3] - launches0
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1404_5756_gb300 import Options, Plan
+
+    w = make_inputs()
+    nvar, nz, ny, nx = w["x"].shape
+    npts = nvar * nz * ny * nx
+    plan3 = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=nz), Options(order=3),
+                 device=dev)
+    plan1 = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=nz),
+                 Options(order=1, iters=5), device=dev)
+    x = torch.from_numpy(w["x"]).to(dev)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- 3rd-RF: the timed region of the headline number
+    barrier()
+    with ClockSampler(local) as clk:
+        total_ms, fwd_ms, adj_ms, launches = timed_loop(torch, plan3, x, y, z, args.steps,
+                                                        args.warmup, stream)
+    barrier()
+    total_ms = max_over_ranks(torch, world, total_ms)
+    ms_step = total_ms / args.steps
+    value = world * 2 * npts / (ms_step * 1e-3) / 1e9
+
+    # ---- 1st-RF x5, same protocol
+    barrier()
+    t1_ms, f1, a1, _ = timed_loop(torch, plan1, x, y, z, args.steps, args.warmup, stream)
+    t1_ms = max_over_ranks(torch, world, t1_ms)
+    value1 = world * 2 * npts / (t1_ms / args.steps * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI on pinned host buffers
+    xh = torch.from_numpy(w["x"]).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    zh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        plan3.apply_host(xh, yh, nvar=nvar)
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan3.apply_host(xh, yh, nvar=nvar)
+        plan3.apply_host(yh, zh, nvar=nvar, adjoint=True)
+    e2e_s = max_over_ranks(torch, world, time.perf_counter() - t0)
+    e2e_val = world * 2 * npts * e2e_steps / e2e_s / 1e9
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of one application (forward) of the dominant operator
+    peak, peak_kind = hbm_peak()
+    plane = nx * ny
+    coef_bytes = 2 * 16 * plane + plane          # x and y coefficients + mask
+    alg_bytes = 8 * npts + coef_bytes            # read + write every point once
+    t_app = float(np.mean(fwd_ms + adj_ms)) * 1e-3
+    achieved = alg_bytes / t_app / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                "traffic": profiled_traffic(),
+                "unit_of_work": "one V_h application (fwd or adjoint) over the batch",
+                "alg_bytes_per_application": alg_bytes,
+                "launches_per_application": launches / (2 * args.steps)}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(w, args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "nz": nz, "nvar": nvar,
+                   "points_per_step": 2 * npts, "l2": "inputs larger than L2 (453 MB field)",
+                   "parallelism": f"replicas/level batches x{world}"},
+        "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
+        "rf1x5": {"value": value1, "unit": "Gpts/s", "ms_per_step": t1_ms / args.steps,
+                  "ms_fwd": float(np.mean(f1)), "ms_adj": float(np.mean(a1))},
+        "speedup_rf3_over_rf1x5": value / value1,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_val, "unit": "Gpts/s",
+                "h2d_bytes_per_step": 2 * 4 * npts, "d2h_bytes_per_step": 2 * 4 * npts},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def max_over_ranks(torch, world, v):
+    if world == 1:
+        return v
+    t = torch.tensor([float(v)], device="cuda")
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,158 @@
+/*
+ * rfvh.h -- C ABI of the GB300 recursive-filter library for the horizontal
+ * background-error covariance operator V_H of an ocean 3D-VAR.
+ *
+ * Method: Farina, Dobricic, Storto, Masina, Cuomo, "A Revised Scheme to
+ * Compute Horizontal Covariances in an Oceanographic 3D-VAR Assimilation
+ * System" (arXiv 1404.5756).  V_H = G_y G_x (Sec. 2.2): a 1-D recursive
+ * filter is applied along every row (x) and then along every column (y) of
+ * every level of every variable.  Each 1-D filter is a causal (forward) pass
+ * followed by an anticausal (backward) pass (Sec. 3, Eqs. "one1"/"two2"):
+ *   - order 3: the third-order filter of Theorem 3.1, one iteration, with
+ *     per-point coefficients from sigma_i = R_i/dx_i;
+ *   - order 1: the first-order filter of Sec. 3.1 iterated K times, with the
+ *     coefficients of Hayden's relation (Eq. "crucial").
+ * Initial conditions are the heuristic zero-state ones of Sec. 3.1.  Coasts
+ * use imaginary sea points (Sec. 1, Sec. 4): each run of sea points of a
+ * line is extended at both ends by n_img = ceil(img_factor * sigma_coast)
+ * points of zero input carrying the coastal point's coefficients; only the
+ * sea points are written.  Land points are written as 0 and their input is
+ * ignored.  rf_apply_adjoint applies V_H^T = G_x^T G_y^T (the transpose the
+ * 3D-VAR gradient of Eq. "eight" needs).
+ *
+ * Conventions for every call:
+ *   - Fields are FP32, laid out [nvar][nz][ny][nx] with x fastest, one
+ *     contiguous array per domain, in device memory.
+ *   - Masks are uint8 [mask_nz][ny][nx] (nonzero = sea); length scales are
+ *     FP32 [L_nz][ny][nx] in grid units (sigma = R/dx).  mask_nz and L_nz
+ *     are 1 (one 2-D field shared by every level) or nz.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Apply calls are asynchronous on it; rf_coeffs synchronises it.
+ *   - No call throws; every call returns an rf_status.  Argument errors are
+ *     reported synchronously, before any GPU work is queued.
+ *   - The caller owns every buffer it passes in; the plan owns every buffer
+ *     it derives (coefficients, boundary maps, work lists, scratch).
+ */
+#ifndef RFVH_H
+#define RFVH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RF_OK = 0,
+    RF_EINVAL = 1,        /* bad argument: null pointer, size, option, length scale */
+    RF_ENOMEM = 2,        /* device or host allocation failed */
+    RF_ECUDA = 3,         /* a CUDA call or kernel launch failed */
+    RF_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    RF_EUNSUPPORTED = 5   /* valid request this build does not provide */
+} rf_status;
+
+enum {
+    RF_NORM_GAUSS_PEAK = 0, /* Theorem 3.1 normalisation: impulse response peaks
+                               near 1, sums to sqrt(2 pi) sigma per direction;
+                               the 1st-RF gets (2 pi sigma^2)^(1/(4K)) per pass */
+    RF_NORM_UNIT_SUM = 1    /* every pass has DC gain 1 (the literal 1st-RF) */
+};
+
+typedef struct rf_plan_ *rf_plan;
+
+/* One domain's grid. */
+typedef struct {
+    int64_t nx, ny, nz;   /* points along x (contiguous), y, and levels     */
+    int64_t mask_nz;      /* 1 or nz                                        */
+    int64_t L_nz;         /* 1 or nz                                        */
+} rf_grid;
+
+typedef struct {
+    int order;            /* 3 (Theorem 3.1) or 1 (Sec. 3.1)                 */
+    int iters;            /* K: must be 1 for order 3, >= 1 for order 1      */
+    double img_factor;    /* imaginary points per coast end = ceil(img_factor
+                             * sigma_coast); 0 = the bare heuristic ICs;
+                             must be finite and >= 0                         */
+    int norm;             /* RF_NORM_GAUSS_PEAK or RF_NORM_UNIT_SUM          */
+    int flags;            /* reserved, must be 0                             */
+    int chunk;            /* reserved tuning override, 0 = automatic         */
+    int tile;             /* reserved tuning override, 0 = automatic         */
+} rf_options;
+
+/* Fill *opt with the defaults: order 3, iters 1, img_factor 3, Gaussian-peak
+ * normalisation.  Returns RF_EINVAL if opt is NULL. */
+rf_status rf_options_default(rf_options *opt);
+
+/* Build a plan for `ndomains` independent domains (a ragged batch).
+ *   grids[d]          grid of domain d (host array of ndomains structs)
+ *   mask[d]           device pointer, uint8 [mask_nz][ny][nx], nonzero = sea
+ *   Lx[d], Ly[d]      device pointers, FP32 [L_nz][ny][nx], length scale
+ *                     along x and along y in grid units; must be finite and
+ *                     > 0 wherever the point is sea on some level
+ *   opt               options (host); NULL means rf_options_default
+ *   stream            cudaStream_t used for the set-up work; synchronised
+ *   out               receives the plan; untouched on error
+ * Computes the per-point coefficients of Theorem 3.1 (order 3) or of Sec.
+ * 3.1 (order 1) in FP64 on the GPU and stores them as FP32, finds the sea
+ * segments of every line and computes, in FP64, the map that takes the
+ * forward state at each segment's last sea point to the backward start state
+ * (the effect of the n_img imaginary points).  The caller's mask and length
+ * scale buffers may be freed once the call returns.
+ * Errors: RF_EINVAL (null pointers, ndomains < 1, nx/ny/nz < 1, mask_nz or
+ * L_nz not in {1, nz}, bad options, invalid length scale at a sea point),
+ * RF_ENOMEM, RF_ECUDA. */
+rf_status rf_coeffs(const rf_grid *grids, int ndomains,
+                    const uint8_t *const *mask, const float *const *Lx,
+                    const float *const *Ly, const rf_options *opt,
+                    void *stream, rf_plan *out);
+
+/* out = V_H in, i.e. G_y G_x on every level of every variable of every
+ * domain (Sec. 2.2; G_x, G_y per Theorem 3.1 or Sec. 3.1 and the plan's
+ * options).
+ *   in[d], out[d]     device pointers to domain d's FP32 field
+ *                     [nvar][nz][ny][nx]; in[d] == out[d] is allowed;
+ *                     distinct domains must not overlap
+ *   nvar              variables per domain (e.g. 2 for T and S), >= 1
+ * Asynchronous on `stream`.  Errors: RF_EINVAL (null plan or pointers,
+ * nvar < 1), RF_ENOMEM (scratch growth), RF_ECUDA (launch failure). */
+rf_status rf_apply(rf_plan p, const float *const *in, float *const *out,
+                   int nvar, void *stream);
+
+/* out = V_H^T in = G_x^T G_y^T in: the exact transpose of rf_apply (the
+ * transposed recursions of each pass, the y direction first).  Same
+ * arguments, ownership and errors as rf_apply. */
+rf_status rf_apply_adjoint(rf_plan p, const float *const *in,
+                           float *const *out, int nvar, void *stream);
+
+/* End-to-end variant of rf_apply / rf_apply_adjoint on HOST buffers: copies
+ * in[d] (host, ideally pinned) to plan-owned device staging, applies V_H
+ * (adjoint != 0: V_H^T), copies the result back into out[d] (host) and
+ * synchronises `stream`.  The staging buffers are allocated on first use
+ * and kept by the plan.  Errors as rf_apply. */
+rf_status rf_apply_host(rf_plan p, const float *const *in, float *const *out,
+                        int nvar, int adjoint, void *stream);
+
+/* Sticky status of the plan: RF_OK, or the first error a launch or a
+ * device-side check recorded since the plan was built. */
+rf_status rf_plan_status(rf_plan p);
+
+/* Counts of the plan: total grid points per variable over all domains
+ * (nx*ny*nz summed), number of domains, device bytes owned by the plan, and
+ * the number of kernels the apply calls have launched since the plan was
+ * built.  Any output pointer may be NULL. */
+rf_status rf_plan_info(rf_plan p, int64_t *points_per_var, int *ndomains,
+                       int64_t *device_bytes, int64_t *launches);
+
+/* Free everything the plan owns (waits for the device first).  NULL is a
+ * no-op returning RF_OK. */
+rf_status rf_plan_destroy(rf_plan p);
+
+/* Static human-readable name of a status code. */
+const char *rf_status_string(rf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RFVH_H */

@@ -1,0 +1,105 @@
+// rf_coef.cuh -- FP64 filter coefficients and coastal boundary maps.
+//
+// Third-order filter (Theorem 3.1): with sigma = R/dx,
+//   a0 = P0 + P1 s + P2 s^2 + s^3,  alpha_j = a_j/a0,
+//   beta = (2 pi s^2)^(1/4) (1 - sum_j alpha_j) = (2 pi s^2)^(1/4) P0/a0,
+// because a0 - a1 - a2 - a3 = P0 exactly for the Theorem's a_j.  The GPU runs
+// the same recursion in its delta (difference) realisation: with
+//   d1_i = p_i - p_{i-1},  d2_i = d1_i - d1_{i-1},
+// writing a_{i,0} p_i - sum_j a_{i,j} p_{i-j} as a polynomial in the backward
+// difference (Appendix A, s = 1 - z^-1) gives, per point,
+//   t   = beta s_i - e p_{i-1} - c1 d1_{i-1} - c2 d2_{i-1}
+//   d2_i = d2_{i-1} + t,  d1_i = d1_{i-1} + d2_i,  p_i = p_{i-1} + d1_i
+// with e = P0/a0, c1 = (P0 + P1 s)/a0, c2 = (P0 + P1 s + P2 s^2)/a0.  This is
+// an exact identity with the direct form, even with per-point coefficients,
+// and keeps FP32 rounding small when 1 - sum alpha is tiny (large sigma).
+// First-order filter (Sec. 3.1, Hayden): E = K/sigma^2, e = 1 - alpha =
+// sqrt(E(E+2)) - E, and the step is p_i = p_{i-1} + (beta s_i - e p_{i-1}).
+#pragma once
+#include <cstdint>
+
+namespace rfvh {
+
+// Theorem 3.1 constants, as printed.
+constexpr double kP0 = 3.738128;
+constexpr double kP1 = 5.788982;
+constexpr double kP2 = 3.382473;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+struct Coef64 {
+    double beta, e, c1, c2;
+};
+
+// Per-point coefficients in FP64 (sigma > 0, finite).  norm: 0 Gaussian peak,
+// 1 unit sum.  For order 1, c1 = c2 = 0.
+__host__ __device__ inline Coef64 coef_fp64(double sigma, int order, int K,
+                                            int norm)
+{
+    Coef64 c;
+    if (order == 3) {
+        double s = sigma;
+        double a0 = kP0 + s * (kP1 + s * (kP2 + s));
+        double inv = 1.0 / a0;
+        c.e = kP0 * inv;
+        c.c1 = (kP0 + kP1 * s) * inv;
+        c.c2 = (kP0 + s * (kP1 + kP2 * s)) * inv;
+        double g = norm == 1 ? 1.0 : sqrt(sqrt(kTwoPi) * s);
+        c.beta = g * c.e;
+    } else {
+        double E = (double)K / (sigma * sigma);
+        double r = sqrt(E * (E + 2.0));
+        c.e = 2.0 * E / (r + E);      // = r - E without cancellation
+        c.c1 = 0.0;
+        c.c2 = 0.0;
+        double g = norm == 1 ? 1.0 : pow(kTwoPi * sigma * sigma, 1.0 / (4.0 * K));
+        c.beta = g * c.e;
+    }
+    return c;
+}
+
+// Boundary map of one coast end.  Running the forward recursion from the
+// state X at the last sea point through n imaginary points (zero input, the
+// coastal coefficients), then the backward recursion from zero state at the
+// far end back to the coast, leaves the backward state Y = M X at the first
+// imaginary point, with (delta basis, A the one-step matrix, b the input
+// column, c = (1,0,0) the output row)
+//   M = sum_{k=1..n} A^{k-1} b c^T A^k.
+// Order 3 writes the 3x3 M row-major into m[0..9); order 1 writes m[0].
+__host__ __device__ inline void tail_map_fp64(double sigma, int n_img, int order,
+                                              int K, int norm, double *m)
+{
+    Coef64 c = coef_fp64(sigma, order, K, norm);
+    if (order == 1) {
+        double a = 1.0 - c.e, acc = 0.0, v = c.beta, w = a;
+        for (int k = 1; k <= n_img; ++k) {
+            acc += v * w;
+            v *= a;
+            w *= a;
+        }
+        m[0] = acc;
+        for (int r = 1; r < 9; ++r) m[r] = 0.0;
+        return;
+    }
+    // one-step matrix acting on (p, d1, d2)
+    const double A[9] = {1.0 - c.e, 1.0 - c.c1, 1.0 - c.c2,
+                         -c.e,      1.0 - c.c1, 1.0 - c.c2,
+                         -c.e,      -c.c1,      1.0 - c.c2};
+    double v[3] = {c.beta, c.beta, c.beta};    // A^{k-1} b
+    double w[3] = {A[0], A[1], A[2]};          // c^T A^k (first row of A^k)
+    for (int r = 0; r < 9; ++r) m[r] = 0.0;
+    for (int k = 1; k <= n_img; ++k) {
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q) m[3 * r + q] += v[r] * w[q];
+        double nv[3], nw[3];
+        for (int r = 0; r < 3; ++r) {
+            nv[r] = A[3 * r] * v[0] + A[3 * r + 1] * v[1] + A[3 * r + 2] * v[2];
+            nw[r] = w[0] * A[r] + w[1] * A[3 + r] + w[2] * A[6 + r];
+        }
+        for (int r = 0; r < 3; ++r) {
+            v[r] = nv[r];
+            w[r] = nw[r];
+        }
+    }
+}
+
+}  // namespace rfvh

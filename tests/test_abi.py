@@ -1,0 +1,95 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function include/rfvh.h declares, and rejects bad
+arguments before queueing any GPU work."""
+import ctypes
+
+import pytest
+
+from paper_1404_5756_gb300 import _lib
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load(build_if_missing=True)
+
+
+def test_header_declares_the_boundary():
+    names = _lib.declared_functions()
+    for n in ["rf_coeffs", "rf_apply", "rf_apply_adjoint", "rf_plan_status",
+              "rf_plan_destroy", "rf_status_string", "rf_options_default",
+              "rf_apply_host", "rf_plan_info"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _lib.declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code in range(6):
+        s = _lib.status_string(code)
+        assert s.startswith("RF_")
+    assert "unknown" in _lib.status_string(99)
+
+
+def test_options_default(lib):
+    o = _lib.rf_options_default()
+    assert (o.order, o.iters, o.img_factor, o.norm, o.flags) == (3, 1, 3.0, 0, 0)
+    assert lib.rf_options_default(None) == _lib.RF_EINVAL
+
+
+def _coeffs(lib, grid, opt, masks=(1,), lx=(1,), ly=(1,), nd=1, out=True):
+    g = (_lib.rf_grid * max(nd, 1))(*([grid] * max(nd, 1)))
+    plan = ctypes.c_void_p()
+    return lib.rf_coeffs(g, nd, _lib.ptr_array(list(masks)), _lib.ptr_array(list(lx)),
+                         _lib.ptr_array(list(ly)),
+                         ctypes.byref(opt) if opt is not None else None, None,
+                         ctypes.byref(plan) if out else None)
+
+
+def test_rf_coeffs_rejects_bad_arguments(lib):
+    ok_grid = _lib.rf_grid(16, 8, 2, 1, 1)
+    opt = _lib.rf_options_default()
+    E = _lib.RF_EINVAL
+    assert _coeffs(lib, ok_grid, opt, nd=0) == E
+    assert _coeffs(lib, ok_grid, opt, out=False) == E
+    assert _coeffs(lib, ok_grid, opt, masks=(None,)) == E
+    assert _coeffs(lib, ok_grid, opt, lx=(None,)) == E
+    for bad in [_lib.rf_grid(0, 8, 2, 1, 1), _lib.rf_grid(16, 8, 0, 1, 1),
+                _lib.rf_grid(16, 8, 3, 2, 1), _lib.rf_grid(16, 8, 3, 1, 2)]:
+        assert _coeffs(lib, bad, opt) == E
+
+    def with_(**kw):
+        o = _lib.rf_options_default()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+    for o in [with_(order=2), with_(order=3, iters=2), with_(order=1, iters=0),
+              with_(img_factor=-1.0), with_(img_factor=float("inf")),
+              with_(img_factor=float("nan")), with_(norm=5), with_(flags=1)]:
+        assert _coeffs(lib, ok_grid, o) == E
+
+
+def test_apply_rejects_bad_arguments(lib):
+    E = _lib.RF_EINVAL
+    arr = _lib.ptr_array([1])
+    assert lib.rf_apply(None, arr, arr, 1, None) == E
+    assert lib.rf_apply_adjoint(None, arr, arr, 1, None) == E
+    assert lib.rf_apply_host(None, arr, arr, 1, 0, None) == E
+    assert lib.rf_plan_status(None) == E
+    assert lib.rf_plan_info(None, None, None, None, None) == E
+    assert lib.rf_plan_destroy(None) == _lib.RF_OK
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The product package never imports the oracle."""
+    import os
+    import re
+    pkg = os.path.dirname(_lib.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(root, f)).read()
+                assert not re.search(r"\boracle\b\s*import|import\s+oracle|from\s+oracle",
+                                     text), f
