@@ -1,8 +1,10 @@
 // rf_plan.cu -- C ABI of the recursive-filter library: plan construction
-// (validation, sea segments, FP64 coefficients and boundary maps) and the
-// apply entry points.  See include/rfvh.h for the contract of every call.
+// (validation, sea segments, FP64 coefficients, coastal boundary maps, chunk
+// transfer matrices) and the apply entry points.  See include/rfvh.h for the
+// contract of every call.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -12,6 +14,7 @@
 #include "rfvh.h"
 #include "rf_coef.cuh"
 #include "rf_line.cuh"
+#include "rf_tile.cuh"
 
 using namespace rfvh;
 
@@ -22,19 +25,30 @@ struct TailSpec {
     int n_img;
 };
 
+// Everything one direction (x: rows, y: columns) of one domain needs.
+struct Dir {
+    int64_t n = 0, nlines = 0;       // line length, lines per slice
+    int64_t pt_stride = 0, line_stride = 0;
+    int64_t C = 0;                   // chunk length of the tile kernel (odd)
+    int R = 0;                       // lines per CTA; 0 = long-line kernel
+    size_t smem = 0;
+    float4 *coef = nullptr;          // [ncl][nlines][n]
+    int32_t *tail_base = nullptr;    // [ncl*nlines + 1] first boundary map of each line
+    double *tmap = nullptr;          // [ntail][9], consecutive along each line
+    float *xfer = nullptr;           // [ncl][nlines][32][XF]
+    float4 *coef_il_base = nullptr;  // interleaved coefficients with guards
+    float4 *coef_il = nullptr;       // [ncl][nlines][C][32] (tile kernel)
+    LaneInfo *lanes = nullptr;       // [ncl][nlines][32]
+    int64_t ntail = 0;
+    int max_re = 0;                  // most segment ends on one line
+};
+
 struct Domain {
     rf_grid g{};
-    int64_t ncl = 1;                 // levels of distinct segment structure
-    uint8_t *mask = nullptr;         // [mask_nz][ny][nx]
-    float4 *coef_x = nullptr;        // [L_nz][ny][nx]
-    float4 *coef_y = nullptr;
-    int32_t *tail_x = nullptr;       // [ncl][ny][nx]
-    int32_t *tail_y = nullptr;
-    double *tmap_x = nullptr;        // [ntail_x][9]
-    double *tmap_y = nullptr;
-    int64_t ntail_x = 0, ntail_y = 0;
-    float *yscr = nullptr;           // backward start states
-    int64_t yscr_floats = 0;
+    int64_t ncl = 1;                 // levels with distinct coefficients
+    Dir d[2];                        // 0: x, 1: y
+    float *tscr = nullptr;           // boundary-map start states
+    int64_t tscr_floats = 0;
     float *stage = nullptr;          // host-API staging
     int64_t stage_floats = 0;
 };
@@ -50,6 +64,9 @@ struct rf_plan_ {
 };
 
 namespace {
+
+constexpr size_t kSmemTarget = 112 * 1024;   // two CTAs per SM
+constexpr size_t kSmemMax = 227 * 1024;
 
 template <class T>
 rf_status dev_alloc(T **p, int64_t count, int64_t *bytes)
@@ -68,14 +85,15 @@ rf_status dev_alloc(T **p, int64_t count, int64_t *bytes)
 
 void free_domain(Domain &d)
 {
-    cudaFree(d.mask);
-    cudaFree(d.coef_x);
-    cudaFree(d.coef_y);
-    cudaFree(d.tail_x);
-    cudaFree(d.tail_y);
-    cudaFree(d.tmap_x);
-    cudaFree(d.tmap_y);
-    cudaFree(d.yscr);
+    for (Dir &q : d.d) {
+        cudaFree(q.coef);
+        cudaFree(q.tail_base);
+        cudaFree(q.tmap);
+        cudaFree(q.xfer);
+        cudaFree(q.coef_il_base);
+        cudaFree(q.lanes);
+    }
+    cudaFree(d.tscr);
     cudaFree(d.stage);
     d = Domain{};
 }
@@ -95,81 +113,9 @@ rf_status check_grid(const rf_grid &g)
     if (g.nx < 1 || g.ny < 1 || g.nz < 1) return RF_EINVAL;
     if (!(g.mask_nz == 1 || g.mask_nz == g.nz)) return RF_EINVAL;
     if (!(g.L_nz == 1 || g.L_nz == g.nz)) return RF_EINVAL;
-    // indices inside the kernels are 64-bit, but a line index times the
-    // slice count must stay well inside int64 and lines inside int32 counts
-    if (g.nx > (1 << 30) || g.ny > (1 << 30) || g.nz > (1 << 20)) return RF_EINVAL;
-    return RF_OK;
-}
-
-// FP64 coefficients on the device, stored as FP32 (beta, e, c1, c2).
-__global__ void coef_kernel(int64_t n, const float *__restrict__ L,
-                            float4 *__restrict__ coef, int order, int K, int norm)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = (double)L[i];
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (s > 0.0 && isfinite(s)) {
-        Coef64 c = coef_fp64(s, order, K, norm);
-        r = make_float4((float)c.beta, (float)c.e, (float)c.c1, (float)c.c2);
-    }
-    coef[i] = r;
-}
-
-__global__ void tail_kernel(int64_t n, const TailSpec *__restrict__ spec,
-                            double *__restrict__ tmap, int order, int K, int norm)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    tail_map_fp64((double)spec[i].sigma, spec[i].n_img, order, K, norm, tmap + 9 * i);
-}
-
-int n_imaginary(double img_factor, float sigma)
-{
-    if (!(img_factor > 0.0)) return 0;
-    return (int)std::ceil(img_factor * (double)sigma);
-}
-
-// Host analysis of one domain: validate length scales at sea points, find
-// the last sea point of every segment of every line, give each one a
-// boundary-map index and record its coastal sigma and imaginary count.
-rf_status analyse(const rf_grid &g, int64_t ncl, const std::vector<uint8_t> &mask,
-                  const std::vector<float> &Lx, const std::vector<float> &Ly,
-                  double img_factor, std::vector<int32_t> &tx,
-                  std::vector<int32_t> &ty, std::vector<TailSpec> &sx,
-                  std::vector<TailSpec> &sy)
-{
-    const int64_t nx = g.nx, ny = g.ny, plane = nx * ny;
-    tx.assign((size_t)(ncl * plane), -1);
-    ty.assign((size_t)(ncl * plane), -1);
-    for (int64_t k = 0; k < ncl; ++k) {
-        const uint8_t *m = mask.data() + (g.mask_nz > 1 ? k : 0) * plane;
-        const float *lx = Lx.data() + (g.L_nz > 1 ? k : 0) * plane;
-        const float *ly = Ly.data() + (g.L_nz > 1 ? k : 0) * plane;
-        for (int64_t p = 0; p < plane; ++p) {
-            if (!m[p]) continue;
-            if (!(lx[p] > 0.f) || !std::isfinite(lx[p])) return RF_EINVAL;
-            if (!(ly[p] > 0.f) || !std::isfinite(ly[p])) return RF_EINVAL;
-        }
-        if (!(img_factor > 0.0)) continue;
-        int32_t *txk = tx.data() + k * plane;
-        int32_t *tyk = ty.data() + k * plane;
-        for (int64_t j = 0; j < ny; ++j)
-            for (int64_t i = 0; i < nx; ++i) {
-                int64_t p = j * nx + i;
-                if (!m[p]) continue;
-                if (i == nx - 1 || !m[p + 1]) {
-                    if (sx.size() >= (size_t)INT32_MAX) return RF_EINVAL;
-                    txk[p] = (int32_t)sx.size();
-                    sx.push_back({lx[p], n_imaginary(img_factor, lx[p])});
-                }
-                if (j == ny - 1 || !m[p + nx]) {
-                    if (sy.size() >= (size_t)INT32_MAX) return RF_EINVAL;
-                    tyk[p] = (int32_t)sy.size();
-                    sy.push_back({ly[p], n_imaginary(img_factor, ly[p])});
-                }
-            }
-    }
+    // nz bounds the y extent of the launch grids (one CTA row per level)
+    if (g.nx > (1 << 30) || g.ny > (1 << 30) || g.nz > 65535) return RF_EINVAL;
+    if (g.nx * g.ny > ((int64_t)1 << 40)) return RF_EINVAL;
     return RF_OK;
 }
 
@@ -186,13 +132,319 @@ rf_status cuda_status(cudaError_t e)
         if (_s != RF_OK) return _s;       \
     } while (0)
 
-rf_status build_domain(rf_plan_ *P, Domain &d, const uint8_t *mask_dev,
+// ------------------------------------------------------------------ set-up
+// Per-point coefficients of one direction in line-major order, computed in
+// FP64 and stored as FP32 (beta, e, c1, c2); land -> (0, 0, 0, 1); the last
+// sea point of a segment gets c2 negated.
+__global__ void coef_lines_kernel(int64_t ncl, int64_t nx, int64_t ny, int along_y,
+                                  const uint8_t *__restrict__ mask, int64_t mask_nz,
+                                  const float *__restrict__ L, int64_t L_nz, int order,
+                                  int K, int norm, float4 *__restrict__ out)
+{
+    const int64_t plane = nx * ny;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= ncl * plane) return;
+    const int64_t lev = idx / plane, r = idx - lev * plane;
+    const int64_t n = along_y ? ny : nx;
+    const int64_t line = r / n, pos = r - line * n;
+    const int64_t j = along_y ? pos : line, i = along_y ? line : pos;
+    const uint8_t *m = mask + (mask_nz > 1 ? lev : 0) * plane;
+    const int64_t p = j * nx + i;
+    float4 c = make_float4(0.f, 0.f, 0.f, 1.f);
+    if (m[p]) {
+        const double s = (double)L[(L_nz > 1 ? lev : 0) * plane + p];
+        const Coef64 k = coef_fp64(s, order, K, norm);
+        c = make_float4((float)k.beta, (float)k.e, (float)k.c1, (float)k.c2);
+        const int64_t pn = along_y ? p + nx : p + 1;
+        if (pos == n - 1 || !m[pn]) c.w = -c.w;
+    }
+    out[idx] = c;
+}
+
+__global__ void tail_kernel(int64_t n, const TailSpec *__restrict__ spec,
+                            double *__restrict__ tmap, int order, int K, int norm)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    tail_map_fp64((double)spec[i].sigma, spec[i].n_img, order, K, norm, tmap + 9 * i);
+}
+
+// One-step matrix of the delta form with the reset factor (rf_steps.cuh),
+// from the stored FP32 coefficients.
+__device__ void step_matrix(const float4 &cf, double *A, int order)
+{
+    const double b = cf.x, e = cf.y, c1 = cf.z, c2 = fabs((double)cf.w);
+    const double g = b != 0.0 ? 1.0 : 0.0;
+    if (order == 1) {
+        A[0] = g - e;
+        return;
+    }
+    A[0] = g - e; A[1] = g - c1; A[2] = 1.0 - c2;
+    A[3] = -e;    A[4] = g - c1; A[5] = 1.0 - c2;
+    A[6] = -e;    A[7] = -c1;    A[8] = 1.0 - c2;
+}
+
+__device__ void mm3(const double *P, const double *Q, double *O)
+{
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            O[3 * r + c] = P[3 * r] * Q[c] + P[3 * r + 1] * Q[3 + c] + P[3 * r + 2] * Q[6 + c];
+}
+
+// Chunk transfer matrices (zero-input maps across one lane's chunk), FP64
+// products stored as FP32: forward causal A_{b-1}..A_a, forward anticausal
+// A_a..A_{b-1} (zero if the chunk holds a segment end), adjoint causal
+// (A_a..A_{b-1})^T, adjoint anticausal (A_{b-1}..A_a)^T (zero if a segment
+// end).  Empty chunks get identities.
+// Lane-interleaved copy of one direction's coefficients for the tile kernel
+// (step j of lane l of a line at [line][j][l], points past the line's end
+// are land), with the segment-end flags moved into per-lane bit masks and
+// the rank of each lane's first segment end on its line.  One warp per line.
+__global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C,
+                                  const float4 *__restrict__ coef, float4 *__restrict__ il,
+                                  LaneInfo *__restrict__ lanes)
+{
+    const int64_t line = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (line >= nlines_total) return;   // whole warps exit together
+    const float4 *src = coef + line * n;
+    float4 *dst = il + line * C * 32 + lane;
+    unsigned long long bits = 0;
+    for (int j = 0; j < C; ++j) {
+        const int64_t k = (int64_t)lane * C + j;
+        float4 c = k < n ? src[k] : make_float4(0.f, 0.f, 0.f, 1.f);
+        if (__float_as_uint(c.w) >> 31) {
+            bits |= 1ull << j;
+            c.w = fabsf(c.w);
+        }
+        dst[(int64_t)j * 32] = c;
+    }
+    const int nre = __popcll(bits);
+    int incl = nre;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    LaneInfo li;
+    li.rebits = bits;
+    li.rank0 = incl - nre;
+    li.nre = nre;
+    lanes[line * 32 + lane] = li;
+}
+
+__global__ void xfer_kernel(int64_t nrec, int64_t n, int64_t C, int order,
+                            const float4 *__restrict__ coef, float *__restrict__ xfer)
+{
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nrec) return;
+    const int64_t line = idx / 32, lane = idx - line * 32;
+    const int64_t a = lane * C, b = min(a + C, n);
+    const float4 *cf = coef + line * n;
+    const int M = order == 3 ? 9 : 1;
+    double F[9], Pa[9], A[9], T[9];
+    for (int k = 0; k < M; ++k) F[k] = Pa[k] = (order == 3) ? ((k % 4 == 0) ? 1.0 : 0.0) : 1.0;
+    bool re = false;
+    for (int64_t k = a; k < b; ++k) {
+        step_matrix(cf[k], A, order);
+        re = re || (__float_as_uint(cf[k].w) >> 31);
+        if (order == 3) {
+            mm3(A, F, T);
+            for (int q = 0; q < 9; ++q) F[q] = T[q];
+            mm3(Pa, A, T);
+            for (int q = 0; q < 9; ++q) Pa[q] = T[q];
+        } else {
+            F[0] *= A[0];
+            Pa[0] *= A[0];
+        }
+    }
+    float *o = xfer + idx * (4 * M);
+    for (int k = 0; k < M; ++k) {
+        const int tr = order == 3 ? (k % 3) * 3 + k / 3 : 0;   // transpose index
+        o[k] = (float)F[k];
+        o[M + k] = re ? 0.f : (float)Pa[k];
+        o[2 * M + k] = (float)Pa[tr];
+        o[3 * M + k] = re ? 0.f : (float)F[tr];
+    }
+}
+
+int n_imaginary(double img_factor, float sigma)
+{
+    if (!(img_factor > 0.0)) return 0;
+    return (int)std::ceil(img_factor * (double)sigma);
+}
+
+// Host analysis of one domain: validate length scales at sea points, then
+// for each direction number the segment ends (last sea point of every run of
+// sea points) consecutively along each line, line after line, level after
+// level.  base[d][lev*nlines + line] is the index of a line's first segment
+// end (base has one extra final entry: the total).
+rf_status analyse(const rf_grid &g, int64_t ncl, const std::vector<uint8_t> &mask,
+                  const std::vector<float> &Lx, const std::vector<float> &Ly,
+                  double img_factor, std::vector<int32_t> base[2],
+                  std::vector<TailSpec> sp[2], int max_re[2])
+{
+    const int64_t nx = g.nx, ny = g.ny, plane = nx * ny;
+    base[0].assign((size_t)(ncl * ny + 1), 0);
+    base[1].assign((size_t)(ncl * nx + 1), 0);
+    max_re[0] = max_re[1] = 0;
+    for (int64_t k = 0; k < ncl; ++k) {
+        const uint8_t *m = mask.data() + (g.mask_nz > 1 ? k : 0) * plane;
+        const float *lx = Lx.data() + (g.L_nz > 1 ? k : 0) * plane;
+        const float *ly = Ly.data() + (g.L_nz > 1 ? k : 0) * plane;
+        for (int64_t p = 0; p < plane; ++p) {
+            if (!m[p]) continue;
+            if (!(lx[p] > 0.f) || !std::isfinite(lx[p])) return RF_EINVAL;
+            if (!(ly[p] > 0.f) || !std::isfinite(ly[p])) return RF_EINVAL;
+        }
+        const bool maps = img_factor > 0.0;
+        for (int64_t j = 0; j < ny; ++j) {          // x lines: rows
+            base[0][(size_t)(k * ny + j)] = (int32_t)sp[0].size();
+            int cnt = 0;
+            for (int64_t i = 0; i < nx && maps; ++i) {
+                const int64_t p = j * nx + i;
+                if (m[p] && (i == nx - 1 || !m[p + 1])) {
+                    sp[0].push_back({lx[p], n_imaginary(img_factor, lx[p])});
+                    ++cnt;
+                }
+            }
+            max_re[0] = std::max(max_re[0], cnt);
+            if (sp[0].size() >= (size_t)INT32_MAX) return RF_EINVAL;
+        }
+        for (int64_t i = 0; i < nx; ++i) {          // y lines: columns
+            base[1][(size_t)(k * nx + i)] = (int32_t)sp[1].size();
+            int cnt = 0;
+            for (int64_t j = 0; j < ny && maps; ++j) {
+                const int64_t p = j * nx + i;
+                if (m[p] && (j == ny - 1 || !m[p + nx])) {
+                    sp[1].push_back({ly[p], n_imaginary(img_factor, ly[p])});
+                    ++cnt;
+                }
+            }
+            max_re[1] = std::max(max_re[1], cnt);
+            if (sp[1].size() >= (size_t)INT32_MAX) return RF_EINVAL;
+        }
+    }
+    base[0].back() = (int32_t)sp[0].size();
+    base[1].back() = (int32_t)sp[1].size();
+    return RF_OK;
+}
+
+int64_t smem_stride(int64_t n)
+{
+    return n + ((4 - n % 32) + 32) % 32;   // row stride = 4 (mod 32) floats
+}
+
+// Chunk length of the tile kernel for line length n (odd, so the lanes'
+// shared-memory accesses fall in distinct banks), or 0 when the line is
+// too long for it.
+void choose_chunk(Dir &q)
+{
+    q.C = (q.n + 31) / 32;
+    if (q.C % 2 == 0) ++q.C;
+    q.R = q.C <= kMaxChunk ? 1 : 0;   // R > 0 marks "tile kernel usable"
+}
+
+// (lines per CTA, slices per thread) pairs the tile kernel is built for, in
+// order of preference.
+struct TileShape {
+    int R, B;
+};
+constexpr TileShape kShapesY[] = {{8, 4}, {8, 2}, {4, 4}, {8, 1}, {4, 2}, {2, 4},
+                                  {4, 1}, {2, 1}, {1, 4}, {1, 1}};
+constexpr TileShape kShapesX[] = {{4, 4}, {8, 4}, {2, 4}, {4, 2}, {8, 2}, {4, 1},
+                                  {8, 1}, {1, 4}, {2, 1}, {1, 1}};
+
+// Pick the tile shape for one launch: the first shape whose shared memory
+// allows two CTAs per SM (else one), with B no larger than the slices a CTA
+// gets.  Returns false if even one line of one slice does not fit.
+bool pick_shape(const Dir &q, bool along_y, int64_t slices_per_cta, TileShape &sh,
+                size_t &smem)
+{
+    const int64_t ss = smem_stride(q.n);
+    for (int pass = 0; pass < 2; ++pass) {
+        const size_t cap = pass == 0 ? kSmemTarget : kSmemMax;
+        for (const TileShape &s : along_y ? kShapesY : kShapesX) {
+            if (s.B > 1 && s.B > slices_per_cta) continue;
+            const size_t bytes = (size_t)tile_smem_bytes(s.R, s.B, ss, q.max_re);
+            if (bytes <= cap) {
+                sh = s;
+                smem = bytes;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
+                    const float *L_dev, const std::vector<int32_t> &base,
+                    const std::vector<TailSpec> &sp, int max_re, cudaStream_t st)
+{
+    const rf_grid &g = D.g;
+    Dir &q = D.d[dir];
+    q.n = dir == 0 ? g.nx : g.ny;
+    q.nlines = dir == 0 ? g.ny : g.nx;
+    q.pt_stride = dir == 0 ? 1 : g.nx;
+    q.line_stride = dir == 0 ? g.nx : 1;
+    q.ntail = (int64_t)sp.size();
+    q.max_re = max_re;
+    choose_chunk(q);
+    const int64_t plane = g.nx * g.ny, ncl = D.ncl;
+    const int o = P->opt.order, K = P->opt.iters, nm = P->opt.norm;
+    const int XS = o == 3 ? 36 : 4;
+
+    RF_TRY(dev_alloc(&q.coef, ncl * plane, &P->bytes));
+    RF_TRY(dev_alloc(&q.tail_base, (int64_t)base.size(), &P->bytes));
+    RF_TRY(dev_alloc(&q.tmap, 9 * q.ntail, &P->bytes));
+    if (q.R > 0) {
+        RF_TRY(dev_alloc(&q.xfer, ncl * q.nlines * 32 * XS, &P->bytes));
+        RF_TRY(dev_alloc(&q.coef_il_base, ncl * q.nlines * q.C * 32 + 2 * kCoefGuard, &P->bytes));
+        RF_TRY(dev_alloc(&q.lanes, ncl * q.nlines * 32, &P->bytes));
+        q.coef_il = q.coef_il_base + kCoefGuard;
+        RF_TRY(cuda_status(cudaMemsetAsync(q.coef_il_base, 0,
+                                           sizeof(float4) * (size_t)(ncl * q.nlines * q.C * 32 +
+                                                                     2 * kCoefGuard), st)));
+    }
+    RF_TRY(cuda_status(cudaMemcpyAsync(q.tail_base, base.data(), base.size() * 4,
+                                       cudaMemcpyHostToDevice, st)));
+    const int64_t npts = ncl * plane;
+    coef_lines_kernel<<<(unsigned)((npts + 255) / 256), 256, 0, st>>>(
+        ncl, g.nx, g.ny, dir, mask_dev, g.mask_nz, L_dev, g.L_nz, o, K, nm, q.coef);
+    RF_TRY(cuda_status(cudaGetLastError()));
+    if (q.R > 0) {
+        const int64_t nrec = ncl * q.nlines * 32;
+        xfer_kernel<<<(unsigned)((nrec + 127) / 128), 128, 0, st>>>(nrec, q.n, q.C, o,
+                                                                      q.coef, q.xfer);
+        RF_TRY(cuda_status(cudaGetLastError()));
+        const int64_t nl = ncl * q.nlines;
+        interleave_kernel<<<(unsigned)((nl + 3) / 4), 128, 0, st>>>(nl, q.n, (int)q.C, q.coef,
+                                                                     q.coef_il, q.lanes);
+        RF_TRY(cuda_status(cudaGetLastError()));
+    }
+    if (!sp.empty()) {
+        TailSpec *dsp = nullptr;
+        int64_t dummy = 0;
+        RF_TRY(dev_alloc(&dsp, (int64_t)sp.size(), &dummy));
+        rf_status s = cuda_status(cudaMemcpyAsync(dsp, sp.data(), sp.size() * sizeof(TailSpec),
+                                                  cudaMemcpyHostToDevice, st));
+        if (s == RF_OK) {
+            tail_kernel<<<(unsigned)((q.ntail + 127) / 128), 128, 0, st>>>(q.ntail, dsp, q.tmap,
+                                                                           o, K, nm);
+            s = cuda_status(cudaGetLastError());
+        }
+        if (s == RF_OK) s = cuda_status(cudaStreamSynchronize(st));
+        cudaFree(dsp);
+        RF_TRY(s);
+    }
+    return RF_OK;
+}
+
+rf_status build_domain(rf_plan_ *P, Domain &D, const uint8_t *mask_dev,
                        const float *Lx_dev, const float *Ly_dev, cudaStream_t st)
 {
-    const rf_grid &g = d.g;
+    const rf_grid &g = D.g;
     const int64_t plane = g.nx * g.ny;
-    const int64_t ncl = (g.mask_nz > 1 || g.L_nz > 1) ? g.nz : 1;
-    d.ncl = ncl;
+    D.ncl = (g.mask_nz > 1 || g.L_nz > 1) ? g.nz : 1;
     std::vector<uint8_t> hm((size_t)(g.mask_nz * plane));
     std::vector<float> hx((size_t)(g.L_nz * plane)), hy((size_t)(g.L_nz * plane));
     RF_TRY(cuda_status(cudaMemcpyAsync(hm.data(), mask_dev, hm.size(),
@@ -203,53 +455,12 @@ rf_status build_domain(rf_plan_ *P, Domain &d, const uint8_t *mask_dev,
                                        cudaMemcpyDeviceToHost, st)));
     RF_TRY(cuda_status(cudaStreamSynchronize(st)));
     for (auto &v : hm) v = v ? 1 : 0;
-
-    std::vector<int32_t> tx, ty;
-    std::vector<TailSpec> sx, sy;
-    RF_TRY(analyse(g, ncl, hm, hx, hy, P->opt.img_factor, tx, ty, sx, sy));
-    d.ntail_x = (int64_t)sx.size();
-    d.ntail_y = (int64_t)sy.size();
-
-    RF_TRY(dev_alloc(&d.mask, g.mask_nz * plane, &P->bytes));
-    RF_TRY(dev_alloc(&d.coef_x, g.L_nz * plane, &P->bytes));
-    RF_TRY(dev_alloc(&d.coef_y, g.L_nz * plane, &P->bytes));
-    RF_TRY(dev_alloc(&d.tail_x, ncl * plane, &P->bytes));
-    RF_TRY(dev_alloc(&d.tail_y, ncl * plane, &P->bytes));
-    RF_TRY(dev_alloc(&d.tmap_x, 9 * d.ntail_x, &P->bytes));
-    RF_TRY(dev_alloc(&d.tmap_y, 9 * d.ntail_y, &P->bytes));
-
-    RF_TRY(cuda_status(cudaMemcpyAsync(d.mask, hm.data(), hm.size(),
-                                       cudaMemcpyHostToDevice, st)));
-    RF_TRY(cuda_status(cudaMemcpyAsync(d.tail_x, tx.data(), tx.size() * 4,
-                                       cudaMemcpyHostToDevice, st)));
-    RF_TRY(cuda_status(cudaMemcpyAsync(d.tail_y, ty.data(), ty.size() * 4,
-                                       cudaMemcpyHostToDevice, st)));
-
-    const int o = P->opt.order, K = P->opt.iters, nm = P->opt.norm;
-    const int64_t nl = g.L_nz * plane;
-    const int blk = 256;
-    coef_kernel<<<(unsigned)((nl + blk - 1) / blk), blk, 0, st>>>(nl, Lx_dev, d.coef_x, o, K, nm);
-    coef_kernel<<<(unsigned)((nl + blk - 1) / blk), blk, 0, st>>>(nl, Ly_dev, d.coef_y, o, K, nm);
-    RF_TRY(cuda_status(cudaGetLastError()));
-
-    for (int dir = 0; dir < 2; ++dir) {
-        const std::vector<TailSpec> &sp = dir == 0 ? sx : sy;
-        double *tm = dir == 0 ? d.tmap_x : d.tmap_y;
-        if (sp.empty()) continue;
-        TailSpec *dsp = nullptr;
-        int64_t dummy = 0;
-        RF_TRY(dev_alloc(&dsp, (int64_t)sp.size(), &dummy));
-        rf_status s = cuda_status(cudaMemcpyAsync(dsp, sp.data(), sp.size() * sizeof(TailSpec),
-                                                  cudaMemcpyHostToDevice, st));
-        if (s == RF_OK) {
-            int64_t n = (int64_t)sp.size();
-            tail_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, dsp, tm, o, K, nm);
-            s = cuda_status(cudaGetLastError());
-        }
-        if (s == RF_OK) s = cuda_status(cudaStreamSynchronize(st));
-        cudaFree(dsp);
-        RF_TRY(s);
-    }
+    std::vector<int32_t> base[2];
+    std::vector<TailSpec> sp[2];
+    int max_re[2];
+    RF_TRY(analyse(g, D.ncl, hm, hx, hy, P->opt.img_factor, base, sp, max_re));
+    RF_TRY(build_dir(P, D, 0, mask_dev, Lx_dev, base[0], sp[0], max_re[0], st));
+    RF_TRY(build_dir(P, D, 1, mask_dev, Ly_dev, base[1], sp[1], max_re[1], st));
     return cuda_status(cudaStreamSynchronize(st));
 }
 
@@ -264,16 +475,121 @@ rf_status ensure(float **buf, int64_t *have, int64_t need, int64_t *bytes)
     return RF_OK;
 }
 
-template <int ORDER, bool ADJ>
-void launch_pass(const LineArgs &a, cudaStream_t st)
+// ------------------------------------------------------------------ apply
+template <int ORDER, bool ADJ, int R, int B>
+void launch_tile(const TileArgs &a, int64_t nlines, int64_t groups, size_t smem,
+                 cudaStream_t st)
 {
-    const int64_t nlines = a.along_x ? a.ny : a.nx;
-    const int64_t threads = nlines * a.nslices;
-    line_kernel<ORDER, ADJ><<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(a);
+    cudaFuncSetAttribute(tile_kernel<ORDER, ADJ, R, B>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((unsigned)((nlines + R - 1) / R), (unsigned)groups);
+    tile_kernel<ORDER, ADJ, R, B><<<grid, 32 * R, smem, st>>>(a);
 }
 
-rf_status apply_impl(rf_plan p, const float *const *in, float *const *out,
-                     int nvar, bool adjoint, cudaStream_t st)
+template <int ORDER, bool ADJ>
+void launch_shape(const TileArgs &a, TileShape sh, int64_t nlines, int64_t groups,
+                  size_t smem, cudaStream_t st)
+{
+#define RF_SHAPE(r, b)                                                           \
+    if (sh.R == r && sh.B == b) {                                                \
+        launch_tile<ORDER, ADJ, r, b>(a, nlines, groups, smem, st);              \
+        return;                                                                  \
+    }
+    RF_SHAPE(8, 4) RF_SHAPE(8, 2) RF_SHAPE(8, 1) RF_SHAPE(4, 4) RF_SHAPE(4, 2)
+    RF_SHAPE(4, 1) RF_SHAPE(2, 4) RF_SHAPE(2, 1) RF_SHAPE(1, 4) RF_SHAPE(1, 1)
+#undef RF_SHAPE
+}
+
+// How one direction of one domain is launched for a given slice count.
+struct LaunchCfg {
+    bool tile = false;     // tile kernel (else the long-line kernel)
+    TileShape sh{0, 0};
+    size_t smem = 0;
+    int64_t groups = 1;    // CTA rows along the slices
+};
+
+// Tile shape: a CTA's slices are the variables of one level when the
+// coefficients differ per level, else the slices are split for about two
+// waves of CTAs.
+LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nslices)
+{
+    LaunchCfg L;
+    if (q.R == 0) return L;
+    const bool along_y = q.pt_stride != 1;
+    if (D.ncl > 1) {
+        L.groups = D.g.nz;
+        L.tile = pick_shape(q, along_y, nslices / D.g.nz, L.sh, L.smem);
+        return L;
+    }
+    L.tile = pick_shape(q, along_y, std::max<int64_t>(1, nslices / 8), L.sh, L.smem);
+    if (L.tile) {
+        const int64_t gx = (q.nlines + L.sh.R - 1) / L.sh.R;
+        const int64_t per_sm = L.smem <= kSmemTarget ? 2 : 1;
+        const int64_t target = 2 * 152 * per_sm;
+        int64_t groups = (target + gx - 1) / gx;
+        groups = std::min<int64_t>(groups, std::max<int64_t>(1, nslices / L.sh.B));
+        L.groups = std::max<int64_t>(1, std::min<int64_t>(groups, 65535));
+    }
+    return L;
+}
+
+template <int ORDER, bool ADJ>
+void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *in,
+                float *out, int64_t nslices, int iters, cudaStream_t st)
+{
+    const int64_t plane = D.g.nx * D.g.ny;
+    const TileShape sh = L.sh;
+    const size_t smem = L.smem;
+    const int64_t groups = L.groups;
+    if (L.tile) {
+        TileArgs a{};
+        a.in = in;
+        a.out = out;
+        a.coef = q.coef_il;
+        a.lanes = q.lanes;
+        a.xfer = q.xfer;
+        a.tail_base = q.tail_base;
+        a.tmap = q.tmap;
+        a.n = q.n;
+        a.nlines = q.nlines;
+        a.C = q.C;
+        a.pt_stride = q.pt_stride;
+        a.line_stride = q.line_stride;
+        a.plane = plane;
+        a.nz = D.g.nz;
+        a.nslices = nslices;
+        a.ncl = D.ncl;
+        a.iters = iters;
+        a.smem_stride = (int)smem_stride(q.n);
+        a.max_re = q.ntail > 0 ? q.max_re : 0;
+        a.vec4 = q.pt_stride == 1 && q.n % 4 == 0 && ((uintptr_t)in % 16) == 0 &&
+                 ((uintptr_t)out % 16) == 0;
+        launch_shape<ORDER, ADJ>(a, sh, q.nlines, groups, smem, st);
+    } else {
+        LineArgs a{};
+        a.in = in;
+        a.out = out;
+        a.coef = q.coef;
+        a.tail_base = q.tail_base;
+        a.tmap = q.tmap;
+        a.tscr = D.tscr;
+        a.n = q.n;
+        a.nlines = q.nlines;
+        a.pt_stride = q.pt_stride;
+        a.line_stride = q.line_stride;
+        a.plane = plane;
+        a.nz = D.g.nz;
+        a.nslices = nslices;
+        a.ntail = q.ntail;
+        a.ncl = D.ncl;
+        a.iters = iters;
+        const int64_t threads = q.nlines * nslices;
+        line_kernel<ORDER, ADJ><<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(a);
+    }
+}
+
+rf_status apply_impl(rf_plan p, const float *const *in, float *const *out, int nvar,
+                     bool adjoint, cudaStream_t st)
 {
     if (!p || !in || !out || nvar < 1) return RF_EINVAL;
     for (size_t d = 0; d < p->dom.size(); ++d)
@@ -281,35 +597,25 @@ rf_status apply_impl(rf_plan p, const float *const *in, float *const *out,
     for (size_t d = 0; d < p->dom.size(); ++d) {
         Domain &D = p->dom[d];
         const int64_t nslices = (int64_t)nvar * D.g.nz;
-        const int64_t nt = D.ntail_x > D.ntail_y ? D.ntail_x : D.ntail_y;
-        rf_status s = ensure(&D.yscr, &D.yscr_floats, nslices * nt * 3, &p->bytes);
+        const LaunchCfg cfg[2] = {launch_cfg(D, D.d[0], nslices), launch_cfg(D, D.d[1], nslices)};
+        // global scratch for segment-end states, only for the long-line path
+        int64_t nt = 0;
+        for (int dir = 0; dir < 2; ++dir)
+            if (!cfg[dir].tile) nt = std::max(nt, D.d[dir].ntail);
+        rf_status s = ensure(&D.tscr, &D.tscr_floats, nslices * nt * 3, &p->bytes);
         if (s != RF_OK) return s;
-        LineArgs a{};
-        a.mask = D.mask;
-        a.yscr = D.yscr;
-        a.nx = D.g.nx;
-        a.ny = D.g.ny;
-        a.nz = D.g.nz;
-        a.nslices = nslices;
-        a.mask_nz = (int)D.g.mask_nz;
-        a.L_nz = (int)D.g.L_nz;
-        a.ncl = (int)D.ncl;
-        a.iters = p->opt.iters;
         for (int pass = 0; pass < 2; ++pass) {
-            const bool along_x = adjoint ? pass == 1 : pass == 0;
-            a.in = pass == 0 ? in[d] : out[d];
-            a.out = out[d];
-            a.along_x = along_x ? 1 : 0;
-            a.coef = along_x ? D.coef_x : D.coef_y;
-            a.tail = along_x ? D.tail_x : D.tail_y;
-            a.tmap = along_x ? D.tmap_x : D.tmap_y;
-            a.ntail = along_x ? D.ntail_x : D.ntail_y;
+            const int dir = adjoint ? 1 - pass : pass;   // forward x then y
+            const float *src = pass == 0 ? in[d] : out[d];
+            const Dir &q = D.d[dir];
+            const LaunchCfg &L = cfg[dir];
+            const int K = p->opt.iters;
             if (p->opt.order == 3) {
-                if (adjoint) launch_pass<3, true>(a, st);
-                else launch_pass<3, false>(a, st);
+                if (adjoint) launch_dir<3, true>(D, q, L, src, out[d], nslices, 1, st);
+                else launch_dir<3, false>(D, q, L, src, out[d], nslices, 1, st);
             } else {
-                if (adjoint) launch_pass<1, true>(a, st);
-                else launch_pass<1, false>(a, st);
+                if (adjoint) launch_dir<1, true>(D, q, L, src, out[d], nslices, K, st);
+                else launch_dir<1, false>(D, q, L, src, out[d], nslices, K, st);
             }
             s = cuda_status(cudaGetLastError());
             if (s != RF_OK) {

@@ -1,0 +1,419 @@
+// rf_tile.cuh -- the main filter kernel: R whole lines per CTA, one warp per
+// line, the 32 lanes of a warp owning consecutive chunks of C points (C odd,
+// 32*C >= n, C <= 64).  Each thread filters B slices of its chunk at once (B
+// independent recursions: instruction-level parallelism, and one coefficient
+// read serves B slices).  The line data of the B slices and the coastal
+// boundary maps of the CTA's lines sit in shared memory; the per-point
+// coefficients are read from global memory in a lane-interleaved layout
+// (step j of all 32 lanes is one contiguous 512-byte row, so every read is
+// coalesced and stays in L1 across the four sweeps).  The chunk carries are
+// resolved with a Kogge-Stone scan of affine maps over the lanes (warp
+// shuffles).  One kernel serves both directions:
+//   x pass: a line is a row, points contiguous in global memory;
+//   y pass: a line is a column, points nx apart; R adjacent columns are
+//           loaded together so each row segment is R*4 contiguous bytes.
+//
+// Per line and slice (a slice is one level of one variable), for each of the
+// K iterations (K = 1 for the third-order filter):
+//   A  causal sweep of every chunk from zero state -> chunk end state
+//   scan of (Phi_chunk, end state) over the lanes -> true state at each chunk
+//   B  causal sweep again from the true state -> causal output (in place);
+//      at the last sea point of a segment the coastal boundary map turns the
+//      final causal state into the anticausal start state (FP64)
+//   C  anticausal sweep from zero state (boundary-map starts included)
+//   scan in the reverse lane order
+//   D  anticausal sweep from the true state -> final output (in place)
+// The forward operator uses the forward steps, the adjoint the transposed
+// steps; the chunk transfer matrices Phi come precomputed from the plan.
+#pragma once
+#include <cstdint>
+
+#include "rf_steps.cuh"
+
+namespace rfvh {
+
+// Per (line, lane) record of the segment ends in the lane's chunk.
+struct LaneInfo {
+    unsigned long long rebits;   // bit j: point lane*C + j ends a segment
+    int rank0;                   // segment ends on the line before this chunk
+    int nre;                     // segment ends in this chunk
+};
+
+struct TileArgs {
+    const float *in;          // field [nslices][...] of this domain
+    float *out;
+    const float4 *coef;       // [ncl][nlines][C][32] interleaved (beta, e, c1, c2 >= 0)
+    const LaneInfo *lanes;    // [ncl][nlines][32]
+    const float *xfer;        // [ncl][nlines][32][XF] chunk transfers
+    const int32_t *tail_base; // [ncl*nlines + 1] index of each line's first boundary map
+    const double *tmap;       // [ntail][9], consecutive along each line
+    int64_t n, nlines;        // line length, lines per slice
+    int64_t pt_stride;        // distance between consecutive points of a line
+    int64_t line_stride;      // distance between consecutive lines
+    int64_t plane;            // floats per slice
+    int64_t nz, nslices;
+    int64_t ncl;              // coefficient levels (1 or nz)
+    int C;                    // chunk length (odd, <= 64)
+    int iters;
+    int smem_stride;          // floats per line row in shared memory
+    int max_re;               // boundary-map slots per line (0: no maps)
+    int vec4;                 // rows 16-byte aligned (x pass)
+};
+
+constexpr int kMaxChunk = 64;
+// float4 guard entries before and after the interleaved coefficient array,
+// so the sweeps may prefetch up to two steps past either end of a chunk
+constexpr int kCoefGuard = 64;
+
+// Transfer record per chunk: order 3 -> four 3x3 row-major matrices
+// (forward causal, forward anticausal, adjoint causal, adjoint anticausal);
+// order 1 -> four scalars.
+template <int ORDER>
+struct XF {
+    static constexpr int size = ORDER == 3 ? 36 : 4;
+    static constexpr int mat = ORDER == 3 ? 9 : 1;
+};
+
+__device__ __forceinline__ void cp_async4(void *s, const void *g)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(g));
+}
+
+__device__ __forceinline__ void cp_async8(void *s, const void *g)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(g));
+}
+
+__device__ __forceinline__ void cp_async16(void *s, const void *g)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(g));
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int ORDER>
+__device__ __forceinline__ void mat_vec(const float *P, const float *v, float *o)
+{
+    if (ORDER == 3) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            o[r] = fmaf(P[3 * r], v[0], fmaf(P[3 * r + 1], v[1], P[3 * r + 2] * v[2]));
+    } else {
+        o[0] = P[0] * v[0];
+    }
+}
+
+template <int ORDER>
+__device__ __forceinline__ void mat_mat(const float *P, const float *Q, float *o)
+{
+    if (ORDER == 3) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                o[3 * r + c] = fmaf(P[3 * r], Q[c], fmaf(P[3 * r + 1], Q[3 + c], P[3 * r + 2] * Q[6 + c]));
+    } else {
+        o[0] = P[0] * Q[0];
+    }
+}
+
+// Exclusive scan of affine maps over the warp, for B slices sharing the maps'
+// linear parts.  Lane l holds x -> P x + v[b].  Forward (REV = false): lane l
+// receives the state entering its chunk from lanes 0..l-1; REV: from lanes
+// 31..l+1.
+template <int ORDER, bool REV, int B>
+__device__ __forceinline__ void warp_scan(float *P, float (*v)[3], int lane)
+{
+    constexpr int M = XF<ORDER>::mat;
+    constexpr int S = ORDER == 3 ? 3 : 1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        float Pn[M], vn[B][S];
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            Pn[k] = REV ? __shfl_down_sync(0xffffffffu, P[k], d) : __shfl_up_sync(0xffffffffu, P[k], d);
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int k = 0; k < S; ++k)
+                vn[b][k] = REV ? __shfl_down_sync(0xffffffffu, v[b][k], d)
+                               : __shfl_up_sync(0xffffffffu, v[b][k], d);
+        const bool take = REV ? (lane + d < 32) : (lane >= d);
+        if (take) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                float nv[S];
+                mat_vec<ORDER>(P, vn[b], nv);
+#pragma unroll
+                for (int k = 0; k < S; ++k) v[b][k] += nv[k];
+            }
+            if (d < 16) {   // the last level's composed map is never used
+                float nP[M];
+                mat_mat<ORDER>(P, Pn, nP);
+#pragma unroll
+                for (int k = 0; k < M; ++k) P[k] = nP[k];
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            const float t = REV ? __shfl_down_sync(0xffffffffu, v[b][k], 1)
+                                : __shfl_up_sync(0xffffffffu, v[b][k], 1);
+            v[b][k] = (REV ? lane == 31 : lane == 0) ? 0.f : t;
+        }
+}
+
+// Shared-memory bytes of the tile kernel.  Layout: 16-byte guard | maps
+// [R][max_re][9] double (padded to 16 bytes) | data [B][R][ss] float |
+// starts [B][R][max_re][3] float | 16-byte guard.  The guards keep the
+// sweeps' one-step-ahead data prefetch (one element past either end of a
+// chunk) inside the allocation.
+__host__ __device__ inline int64_t tile_smem_bytes(int64_t R, int64_t B, int64_t ss,
+                                                   int64_t max_re)
+{
+    const int64_t maps = (R * max_re * 9 + 1) / 2 * 2;
+    return 16 + maps * 8 + B * R * ss * 4 + B * R * max_re * 12 + 16;
+}
+
+// One sweep over a lane's chunk for B slices.  cp points at the chunk's
+// first coefficient (consecutive steps 32 float4 apart), dp[b] at slice b's
+// first data value, len points.  CAUSAL walks up, else down.  IN_SEA zeroes
+// the input at land (first read of the data); WRITE stores the outputs in
+// place.  rebits marks segment ends (bit j <-> point j).  In a causal sweep
+// with TAILS the boundary map turns the state after a segment end into the
+// anticausal start state (stored at ys[b] + 3*rank, rank counting up from
+// rk); in an anticausal sweep the state is reset to that stored start state
+// before the segment end is stepped (rank counting down from rk), or to zero
+// without maps.  Coefficients are fetched two steps ahead and data one step
+// ahead, so memory latency overlaps the arithmetic.
+template <int ORDER, bool ADJ, int B, bool CAUSAL, bool IN_SEA, bool WRITE, bool TAILS>
+__device__ __forceinline__ void sweep(const float4 *__restrict__ cp, float *const *dp, int len,
+                                      uint64_t rebits, const double *ml, float *const *ys,
+                                      int rk, float (*st)[3])
+{
+    constexpr int NS = ORDER == 3 ? 3 : 1;
+    if (len <= 0) return;   // empty chunk: touch no memory
+    const int dir = CAUSAL ? 1 : -1;
+    int j = CAUSAL ? 0 : len - 1;
+    int re_next;
+    if (CAUSAL) re_next = rebits ? __ffsll((long long)rebits) - 1 : 64;
+    else re_next = rebits ? 63 - __clzll((long long)rebits) : -1;
+    float4 c = __ldg(cp + 32 * j);
+    float4 c1 = __ldg(cp + 32 * (j + dir));
+    float x[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) x[b] = dp[b][j];
+#pragma unroll 2
+    for (int t = 0; t < len; ++t, j += dir) {
+        const float4 c2 = __ldg(cp + 32 * (j + 2 * dir));
+        float xn[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) xn[b] = dp[b][j + dir];
+        const bool sea = c.x != 0.f;
+        const float g = sea ? 1.f : 0.f;
+        const bool at_end = j == re_next;
+        if (!CAUSAL && at_end) {
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+#pragma unroll
+                for (int q = 0; q < NS; ++q) st[b][q] = TAILS ? ys[b][3 * rk + q] : 0.f;
+            if (TAILS) --rk;
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const float in = IN_SEA ? (sea ? x[b] : 0.f) : x[b];
+            const float y = step<ORDER, ADJ>(in, c, g, st[b]);
+            if (WRITE) dp[b][j] = y;
+        }
+        if (CAUSAL && TAILS && at_end) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) apply_tail<ORDER, ADJ>(ml + 9 * rk, st[b], ys[b] + 3 * rk);
+            ++rk;
+        }
+        if (at_end) {
+            if (CAUSAL) {
+                rebits &= rebits - 1;
+                re_next = rebits ? __ffsll((long long)rebits) - 1 : 64;
+            } else {
+                rebits &= ~((uint64_t)1 << j);
+                re_next = rebits ? 63 - __clzll((long long)rebits) : -1;
+            }
+        }
+        c = c1;
+        c1 = c2;
+#pragma unroll
+        for (int b = 0; b < B; ++b) x[b] = xn[b];
+    }
+}
+
+template <int ORDER, bool ADJ, int R, int B>
+__global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int XS = XF<ORDER>::size, M = XF<ORDER>::mat;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = (int)a.n, C = a.C, ss = a.smem_stride, mre = a.max_re;
+    double *ms = reinterpret_cast<double *>(smem_raw + 16);
+    float *ds = reinterpret_cast<float *>(ms + ((R * mre * 9 + 1) & ~1));
+    float *ys = ds + B * R * ss;
+    const int64_t line0 = (int64_t)blockIdx.x * R;
+    const int64_t myline = line0 + warp;
+    const bool active = myline < a.nlines;
+    const int lines_here = (int)min((int64_t)R, a.nlines - line0);
+
+    // slices handled by this CTA, slice(i) = s_first + i * s_step; all share
+    // one coefficient level
+    const int64_t group = blockIdx.y;
+    int64_t s_first, s_step, s_count, lev;
+    if (a.ncl == 1) {
+        s_first = group;
+        s_step = gridDim.y;
+        s_count = (a.nslices - group + gridDim.y - 1) / gridDim.y;
+        lev = 0;
+    } else {
+        s_first = group;          // level k = group; slices v*nz + k
+        s_step = a.nz;
+        s_count = a.nslices / a.nz;
+        lev = group;
+    }
+    const int64_t lvl_lines = lev * a.nlines;
+
+    // boundary maps of the R lines
+    if (mre > 0) {
+        for (int r = 0; r < lines_here; ++r) {
+            const int64_t base = a.tail_base[lvl_lines + line0 + r];
+            const int cnt = (int)(a.tail_base[lvl_lines + line0 + r + 1] - base);
+            const double *g = a.tmap + 9 * base;
+            double *s = ms + r * mre * 9;
+            for (int q = threadIdx.x; q < cnt * 9; q += blockDim.x) cp_async8(s + q, g + q);
+        }
+    }
+    // my chunk [ka, kb); lanes past the line's end get an empty chunk at n
+    const int ka = min(lane * C, n), kb = min(ka + C, n), len = kb - ka;
+    const float4 *cg = a.coef + ((lvl_lines + min(myline, a.nlines - 1)) * C) * 32 + lane;
+    const double *ml = ms + warp * mre * 9;
+    uint64_t rebits = 0;
+    int rank0 = 0, nre = 0;
+    float Pc[M], Pa[M];
+    if (active) {
+        const LaneInfo li = a.lanes[(lvl_lines + myline) * 32 + lane];
+        rebits = li.rebits;
+        rank0 = li.rank0;
+        nre = li.nre;
+        const float *x = a.xfer + ((lvl_lines + myline) * 32 + lane) * XS;
+        const int oc = ADJ ? 2 : 0, oa = ADJ ? 3 : 1;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            Pc[k] = x[oc * M + k];
+            Pa[k] = x[oa * M + k];
+        }
+    }
+    float *dl[B], *yl[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        dl[b] = ds + (b * R + warp) * ss + ka;
+        yl[b] = ys + (b * R + warp) * mre * 3;
+    }
+    // load/store mapping: the x pass copies rows (16-byte pieces when
+    // aligned), the y pass copies R-column strips, thread t owning column
+    // r = t % R and rows t / R + 32 m
+    const int yr = threadIdx.x % R, yk0 = threadIdx.x / R;
+    const int64_t row_step = 32 * a.pt_stride;
+    const bool maps = mre > 0;
+
+    for (int64_t i0 = 0; i0 < s_count; i0 += B) {
+        const int nb = (int)min((int64_t)B, s_count - i0);
+        // ---- load the lines of nb slices into shared memory
+        for (int b = 0; b < nb; ++b) {
+            const float *src = a.in + (s_first + (i0 + b) * s_step) * a.plane;
+            float *db = ds + b * R * ss;
+            if (a.pt_stride == 1) {
+                for (int r = 0; r < lines_here; ++r) {
+                    const float *g = src + (line0 + r) * a.line_stride;
+                    float *s = db + r * ss;
+                    if (a.vec4) {
+                        for (int q = threadIdx.x; q < n / 4; q += blockDim.x)
+                            cp_async16(s + 4 * q, g + 4 * q);
+                    } else {
+                        for (int k = threadIdx.x; k < n; k += blockDim.x) cp_async4(s + k, g + k);
+                    }
+                }
+            } else if (yr < lines_here) {
+                const float *g = src + (line0 + yr) + (int64_t)yk0 * a.pt_stride;
+                float *s = db + yr * ss;
+                for (int k = yk0; k < n; k += 32, g += row_step) cp_async4(s + k, g);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (active) {
+            for (int it = 0; it < a.iters; ++it) {
+                float st[B][3], v[B][3], P[M];
+                // ---- A: causal, zero start -> chunk end state (land input ignored)
+#pragma unroll
+                for (int b = 0; b < B; ++b) st[b][0] = st[b][1] = st[b][2] = 0.f;
+                sweep<ORDER, ADJ, B, true, true, false, false>(cg, dl, len, 0, ml, yl, 0, st);
+#pragma unroll
+                for (int b = 0; b < B; ++b) v[b][0] = st[b][0], v[b][1] = st[b][1], v[b][2] = st[b][2];
+#pragma unroll
+                for (int k = 0; k < M; ++k) P[k] = Pc[k];
+                warp_scan<ORDER, false, B>(P, v, lane);
+                // ---- B: causal from the true entering state, in place
+#pragma unroll
+                for (int b = 0; b < B; ++b) st[b][0] = v[b][0], st[b][1] = v[b][1], st[b][2] = v[b][2];
+                if (maps) sweep<ORDER, ADJ, B, true, true, true, true>(cg, dl, len, rebits, ml, yl, rank0, st);
+                else sweep<ORDER, ADJ, B, true, true, true, false>(cg, dl, len, rebits, ml, yl, rank0, st);
+                // ---- C: anticausal from zero at the chunk end
+#pragma unroll
+                for (int b = 0; b < B; ++b) st[b][0] = st[b][1] = st[b][2] = 0.f;
+                if (maps) sweep<ORDER, ADJ, B, false, false, false, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
+                else sweep<ORDER, ADJ, B, false, false, false, false>(cg, dl, len, rebits, ml, yl, 0, st);
+#pragma unroll
+                for (int b = 0; b < B; ++b) v[b][0] = st[b][0], v[b][1] = st[b][1], v[b][2] = st[b][2];
+#pragma unroll
+                for (int k = 0; k < M; ++k) P[k] = Pa[k];
+                warp_scan<ORDER, true, B>(P, v, lane);
+                // ---- D: anticausal from the true entering state, in place
+#pragma unroll
+                for (int b = 0; b < B; ++b) st[b][0] = v[b][0], st[b][1] = v[b][1], st[b][2] = v[b][2];
+                if (maps) sweep<ORDER, ADJ, B, false, false, true, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
+                else sweep<ORDER, ADJ, B, false, false, true, false>(cg, dl, len, rebits, ml, yl, 0, st);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // ---- store
+        for (int b = 0; b < nb; ++b) {
+            float *dst = a.out + (s_first + (i0 + b) * s_step) * a.plane;
+            const float *db = ds + b * R * ss;
+            if (a.pt_stride == 1) {
+                for (int r = 0; r < lines_here; ++r) {
+                    float *g = dst + (line0 + r) * a.line_stride;
+                    const float *s = db + r * ss;
+                    if (a.vec4) {
+                        for (int q = threadIdx.x; q < n / 4; q += blockDim.x)
+                            reinterpret_cast<float4 *>(g)[q] = reinterpret_cast<const float4 *>(s)[q];
+                    } else {
+                        for (int k = threadIdx.x; k < n; k += blockDim.x) g[k] = s[k];
+                    }
+                }
+            } else if (yr < lines_here) {
+                float *g = dst + (line0 + yr) + (int64_t)yk0 * a.pt_stride;
+                const float *s = db + yr * ss;
+                for (int k = yk0; k < n; k += 32, g += row_step) *g = s[k];
+            }
+        }
+        __syncthreads();   // stores read ds before the next slices' copies land
+    }
+}
+
+}  // namespace rfvh

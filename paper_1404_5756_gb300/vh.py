@@ -56,6 +56,8 @@ class Plan:
         self.device = torch.device(device)
         if self.device.type != "cuda":
             raise ValueError("Plan needs a CUDA device: the filter has no CPU path")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         _lib.load()
         grids, masks, lxs, lys, keep = [], [], [], [], []
         self.shapes = []
