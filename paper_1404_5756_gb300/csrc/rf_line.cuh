@@ -42,9 +42,9 @@ __global__ void __launch_bounds__(128) line_kernel(LineArgs a)
         for (int64_t k = 0; k < n; ++k) {
             float4 c = cf[k];
             const bool re = right_end(c);
-            c.w = fabsf(c.w);
+            c.x = fabsf(c.x);
             const float x = c.x != 0.f ? src[k * ps] : 0.f;
-            out[k * ps] = step<ORDER, ADJ>(x, c, reset_factor(c), st);
+            out[k * ps] = step<ORDER, ADJ>(x, c, st);
             if (re && a.ntail > 0) {
                 apply_tail<ORDER, ADJ>(a.tmap + 9 * rk, st, scr + 3 * rk);
                 ++rk;
@@ -62,9 +62,9 @@ __global__ void __launch_bounds__(128) line_kernel(LineArgs a)
                 } else {
                     st[0] = st[1] = st[2] = 0.f;
                 }
-                c.w = fabsf(c.w);
+                c.x = fabsf(c.x);
             }
-            out[k * ps] = step<ORDER, ADJ>(out[k * ps], c, reset_factor(c), st);
+            out[k * ps] = step<ORDER, ADJ>(out[k * ps], c, st);
         }
     }
 }

@@ -134,8 +134,8 @@ rf_status cuda_status(cudaError_t e)
 
 // ------------------------------------------------------------------ set-up
 // Per-point coefficients of one direction in line-major order, computed in
-// FP64 and stored as FP32 (beta, e, c1, c2); land -> (0, 0, 0, 1); the last
-// sea point of a segment gets c2 negated.
+// FP64 and stored as FP32 (beta, -e, -c1, -c2); land -> (0, 0, 0, -1); the
+// last sea point of a segment gets beta negated.
 __global__ void coef_lines_kernel(int64_t ncl, int64_t nx, int64_t ny, int along_y,
                                   const uint8_t *__restrict__ mask, int64_t mask_nz,
                                   const float *__restrict__ L, int64_t L_nz, int order,
@@ -150,13 +150,13 @@ __global__ void coef_lines_kernel(int64_t ncl, int64_t nx, int64_t ny, int along
     const int64_t j = along_y ? pos : line, i = along_y ? line : pos;
     const uint8_t *m = mask + (mask_nz > 1 ? lev : 0) * plane;
     const int64_t p = j * nx + i;
-    float4 c = make_float4(0.f, 0.f, 0.f, 1.f);
+    float4 c = make_float4(0.f, 0.f, 0.f, -1.f);
     if (m[p]) {
         const double s = (double)L[(L_nz > 1 ? lev : 0) * plane + p];
         const Coef64 k = coef_fp64(s, order, K, norm);
-        c = make_float4((float)k.beta, (float)k.e, (float)k.c1, (float)k.c2);
+        c = make_float4((float)k.beta, -(float)k.e, -(float)k.c1, -(float)k.c2);
         const int64_t pn = along_y ? p + nx : p + 1;
-        if (pos == n - 1 || !m[pn]) c.w = -c.w;
+        if (pos == n - 1 || !m[pn]) c.x = -c.x;
     }
     out[idx] = c;
 }
@@ -173,7 +173,7 @@ __global__ void tail_kernel(int64_t n, const TailSpec *__restrict__ spec,
 // from the stored FP32 coefficients.
 __device__ void step_matrix(const float4 &cf, double *A, int order)
 {
-    const double b = cf.x, e = cf.y, c1 = cf.z, c2 = fabs((double)cf.w);
+    const double b = fabs((double)cf.x), e = -cf.y, c1 = -cf.z, c2 = -cf.w;
     const double g = b != 0.0 ? 1.0 : 0.0;
     if (order == 1) {
         A[0] = g - e;
@@ -191,11 +191,6 @@ __device__ void mm3(const double *P, const double *Q, double *O)
             O[3 * r + c] = P[3 * r] * Q[c] + P[3 * r + 1] * Q[3 + c] + P[3 * r + 2] * Q[6 + c];
 }
 
-// Chunk transfer matrices (zero-input maps across one lane's chunk), FP64
-// products stored as FP32: forward causal A_{b-1}..A_a, forward anticausal
-// A_a..A_{b-1} (zero if the chunk holds a segment end), adjoint causal
-// (A_a..A_{b-1})^T, adjoint anticausal (A_{b-1}..A_a)^T (zero if a segment
-// end).  Empty chunks get identities.
 // Lane-interleaved copy of one direction's coefficients for the tile kernel
 // (step j of lane l of a line at [line][j][l], points past the line's end
 // are land), with the segment-end flags moved into per-lane bit masks and
@@ -212,10 +207,10 @@ __global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C,
     unsigned long long bits = 0;
     for (int j = 0; j < C; ++j) {
         const int64_t k = (int64_t)lane * C + j;
-        float4 c = k < n ? src[k] : make_float4(0.f, 0.f, 0.f, 1.f);
-        if (__float_as_uint(c.w) >> 31) {
+        float4 c = k < n ? src[k] : make_float4(0.f, 0.f, 0.f, -1.f);
+        if (__float_as_uint(c.x) >> 31) {
             bits |= 1ull << j;
-            c.w = fabsf(c.w);
+            c.x = fabsf(c.x);
         }
         dst[(int64_t)j * 32] = c;
     }
@@ -232,6 +227,11 @@ __global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C,
     lanes[line * 32 + lane] = li;
 }
 
+// Chunk transfer matrices (zero-input maps across one lane's chunk), FP64
+// products stored as FP32: forward causal A_{b-1}..A_a, forward anticausal
+// A_a..A_{b-1} (zero if the chunk holds a segment end), adjoint causal
+// (A_a..A_{b-1})^T, adjoint anticausal (A_{b-1}..A_a)^T (zero if a segment
+// end).  Empty chunks get identities.
 __global__ void xfer_kernel(int64_t nrec, int64_t n, int64_t C, int order,
                             const float4 *__restrict__ coef, float *__restrict__ xfer)
 {
@@ -246,7 +246,7 @@ __global__ void xfer_kernel(int64_t nrec, int64_t n, int64_t C, int order,
     bool re = false;
     for (int64_t k = a; k < b; ++k) {
         step_matrix(cf[k], A, order);
-        re = re || (__float_as_uint(cf[k].w) >> 31);
+        re = re || (__float_as_uint(cf[k].x) >> 31);
         if (order == 3) {
             mm3(A, F, T);
             for (int q = 0; q < 9; ++q) F[q] = T[q];
@@ -527,7 +527,7 @@ LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nslices)
         const int64_t per_sm = L.smem <= kSmemTarget ? 2 : 1;
         const int64_t target = 2 * 152 * per_sm;
         int64_t groups = (target + gx - 1) / gx;
-        groups = std::min<int64_t>(groups, std::max<int64_t>(1, nslices / L.sh.B));
+        groups = std::min<int64_t>(groups, (nslices + L.sh.B - 1) / L.sh.B);
         L.groups = std::max<int64_t>(1, std::min<int64_t>(groups, 65535));
     }
     return L;

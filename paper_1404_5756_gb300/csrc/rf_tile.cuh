@@ -42,7 +42,7 @@ struct LaneInfo {
 struct TileArgs {
     const float *in;          // field [nslices][...] of this domain
     float *out;
-    const float4 *coef;       // [ncl][nlines][C][32] interleaved (beta, e, c1, c2 >= 0)
+    const float4 *coef;       // [ncl][nlines][C][32] interleaved (beta, -e, -c1, -c2)
     const LaneInfo *lanes;    // [ncl][nlines][32]
     const float *xfer;        // [ncl][nlines][32][XF] chunk transfers
     const int32_t *tail_base; // [ncl*nlines + 1] index of each line's first boundary map
@@ -173,9 +173,9 @@ __device__ __forceinline__ void warp_scan(float *P, float (*v)[3], int lane)
 }
 
 // Shared-memory bytes of the tile kernel.  Layout: 16-byte guard | maps
-// [R][max_re][9] double (padded to 16 bytes) | data [B][R][ss] float |
-// starts [B][R][max_re][3] float | 16-byte guard.  The guards keep the
-// sweeps' one-step-ahead data prefetch (one element past either end of a
+// [R][max_re][9] double (padded to 16 bytes) | data [B/W][R][ss] units of W
+// slices | starts [B][R][max_re][3] float | 16-byte guard.  The guards keep
+// the sweeps' one-step-ahead data prefetch (one element past either end of a
 // chunk) inside the allocation.
 __host__ __device__ inline int64_t tile_smem_bytes(int64_t R, int64_t B, int64_t ss,
                                                    int64_t max_re)
@@ -184,23 +184,45 @@ __host__ __device__ inline int64_t tile_smem_bytes(int64_t R, int64_t B, int64_t
     return 16 + maps * 8 + B * R * ss * 4 + B * R * max_re * 12 + 16;
 }
 
+// B slices per thread travel as U = B/W lane values of W slices each: pairs
+// (packed FP32x2 arithmetic) when B is even.
+template <int B>
+struct Pack {
+    static constexpr int W = B % 2 == 0 ? 2 : 1;
+    static constexpr int U = B / W;
+};
+template <int W>
+struct LaneT;
+template <>
+struct LaneT<1> {
+    using L = V1;
+};
+template <>
+struct LaneT<2> {
+    using L = V2;
+};
+
 // One sweep over a lane's chunk for B slices.  cp points at the chunk's
-// first coefficient (consecutive steps 32 float4 apart), dp[b] at slice b's
-// first data value, len points.  CAUSAL walks up, else down.  IN_SEA zeroes
-// the input at land (first read of the data); WRITE stores the outputs in
-// place.  rebits marks segment ends (bit j <-> point j).  In a causal sweep
-// with TAILS the boundary map turns the state after a segment end into the
-// anticausal start state (stored at ys[b] + 3*rank, rank counting up from
-// rk); in an anticausal sweep the state is reset to that stored start state
-// before the segment end is stepped (rank counting down from rk), or to zero
-// without maps.  Coefficients are fetched two steps ahead and data one step
-// ahead, so memory latency overlaps the arithmetic.
+// first coefficient (consecutive steps 32 float4 apart), dp[u] at lane value
+// u's first data element, len points.  CAUSAL walks up, else down.  IN_SEA
+// zeroes the input at land and writes the zero back (first read of the
+// data); WRITE stores the outputs in place.  rebits marks segment ends (bit
+// j <-> point j).  In a causal sweep with TAILS the boundary map turns the
+// state after a segment end into the anticausal start state (stored at
+// ys[b] + 3*rank, rank counting up from rk); in an anticausal sweep the state
+// is reset to that stored start state before the segment end is stepped
+// (rank counting down from rk), or to zero without maps.  Coefficients are
+// fetched two steps ahead and data one step ahead, so memory latency
+// overlaps the arithmetic.
 template <int ORDER, bool ADJ, int B, bool CAUSAL, bool IN_SEA, bool WRITE, bool TAILS>
-__device__ __forceinline__ void sweep(const float4 *__restrict__ cp, float *const *dp, int len,
-                                      uint64_t rebits, const double *ml, float *const *ys,
-                                      int rk, float (*st)[3])
+__device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
+                                      typename LaneT<Pack<B>::W>::L::T *const *dp, int len,
+                                      uint64_t rebits, const double *ml, float *const *ys, int rk,
+                                      typename LaneT<Pack<B>::W>::L::T (*st)[3])
 {
-    constexpr int NS = ORDER == 3 ? 3 : 1;
+    constexpr int W = Pack<B>::W, U = Pack<B>::U, NS = ORDER == 3 ? 3 : 1;
+    using L = typename LaneT<W>::L;
+    using T = typename L::T;
     if (len <= 0) return;   // empty chunk: touch no memory
     const int dir = CAUSAL ? 1 : -1;
     int j = CAUSAL ? 0 : len - 1;
@@ -209,34 +231,49 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp, float *cons
     else re_next = rebits ? 63 - __clzll((long long)rebits) : -1;
     float4 c = __ldg(cp + 32 * j);
     float4 c1 = __ldg(cp + 32 * (j + dir));
-    float x[B];
+    T x[U];
 #pragma unroll
-    for (int b = 0; b < B; ++b) x[b] = dp[b][j];
+    for (int u = 0; u < U; ++u) x[u] = dp[u][j];
 #pragma unroll 2
     for (int t = 0; t < len; ++t, j += dir) {
         const float4 c2 = __ldg(cp + 32 * (j + 2 * dir));
-        float xn[B];
+        T xn[U];
 #pragma unroll
-        for (int b = 0; b < B; ++b) xn[b] = dp[b][j + dir];
+        for (int u = 0; u < U; ++u) xn[u] = dp[u][j + dir];
         const bool sea = c.x != 0.f;
-        const float g = sea ? 1.f : 0.f;
+        const CoefV<L> cv(c, sea ? 1.f : 0.f);
         const bool at_end = j == re_next;
         if (!CAUSAL && at_end) {
 #pragma unroll
-            for (int b = 0; b < B; ++b)
+            for (int u = 0; u < U; ++u)
 #pragma unroll
-                for (int q = 0; q < NS; ++q) st[b][q] = TAILS ? ys[b][3 * rk + q] : 0.f;
+                for (int q = 0; q < NS; ++q) {
+                    float v[W];
+#pragma unroll
+                    for (int h = 0; h < W; ++h) v[h] = TAILS ? ys[u * W + h][3 * rk + q] : 0.f;
+                    st[u][q] = L::make(v);
+                }
             if (TAILS) --rk;
         }
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const float in = IN_SEA ? (sea ? x[b] : 0.f) : x[b];
-            const float y = step<ORDER, ADJ>(in, c, g, st[b]);
-            if (WRITE) dp[b][j] = y;
+        for (int u = 0; u < U; ++u) {
+            T in = x[u];
+            if (IN_SEA && !sea) {
+                in = L::zero();
+                dp[u][j] = in;
+            }
+            const T y = stepv<L, ORDER, ADJ>(in, cv, st[u]);
+            if (WRITE) dp[u][j] = y;
         }
         if (CAUSAL && TAILS && at_end) {
+            // record the final causal state; the boundary maps are applied
+            // afterwards by the whole warp (apply_line_tails)
 #pragma unroll
-            for (int b = 0; b < B; ++b) apply_tail<ORDER, ADJ>(ml + 9 * rk, st[b], ys[b] + 3 * rk);
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int h = 0; h < W; ++h)
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) ys[u * W + h][3 * rk + q] = L::get(st[u][q], h);
             ++rk;
         }
         if (at_end) {
@@ -251,8 +288,32 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp, float *cons
         c = c1;
         c1 = c2;
 #pragma unroll
-        for (int b = 0; b < B; ++b) x[b] = xn[b];
+        for (int u = 0; u < U; ++u) x[u] = xn[u];
     }
+}
+
+// Coastal boundary maps of one line, applied by the whole warp after the
+// causal sweep: for every segment end q of the line (lanes take q = lane,
+// lane + 32, ...) and every slice b, replace the recorded causal state X at
+// ys[b] + 3q by the anticausal start state M_q X (adjoint: M_q^T X), in FP64.
+// Spreading the segment ends over the lanes keeps the FP64 work out of the
+// divergent per-point loop.
+template <int ORDER, bool ADJ, int B>
+__device__ __forceinline__ void apply_line_tails(const double *ml, float *const *ys, int nre_line,
+                                                 int lane)
+{
+    constexpr int NS = ORDER == 3 ? 3 : 1;
+    __syncwarp();
+    for (int q = lane; q < nre_line; q += 32) {
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            float X[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < NS; ++k) X[k] = ys[b][3 * q + k];
+            apply_tail<ORDER, ADJ>(ml + 9 * q, X, ys[b] + 3 * q);
+        }
+    }
+    __syncwarp();
 }
 
 template <int ORDER, bool ADJ, int R, int B>
@@ -260,6 +321,9 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int XS = XF<ORDER>::size, M = XF<ORDER>::mat;
+    constexpr int W = Pack<B>::W, U = Pack<B>::U;
+    using L = typename LaneT<W>::L;
+    using T = typename L::T;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = (int)a.n, C = a.C, ss = a.smem_stride, mre = a.max_re;
     double *ms = reinterpret_cast<double *>(smem_raw + 16);
@@ -270,21 +334,14 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     const bool active = myline < a.nlines;
     const int lines_here = (int)min((int64_t)R, a.nlines - line0);
 
-    // slices handled by this CTA, slice(i) = s_first + i * s_step; all share
-    // one coefficient level
-    const int64_t group = blockIdx.y;
-    int64_t s_first, s_step, s_count, lev;
-    if (a.ncl == 1) {
-        s_first = group;
-        s_step = gridDim.y;
-        s_count = (a.nslices - group + gridDim.y - 1) / gridDim.y;
-        lev = 0;
-    } else {
-        s_first = group;          // level k = group; slices v*nz + k
-        s_step = a.nz;
-        s_count = a.nslices / a.nz;
-        lev = group;
-    }
+    // Slices handled by this CTA, in groups of B sharing one coefficient
+    // level.  One level for every slice: group g holds slices g*B + b and the
+    // CTA row y takes groups y, y + rows, ...  Per-level coefficients: CTA
+    // row y is level y, its groups hold the variables v0 + b of that level.
+    const bool one_level = a.ncl == 1;
+    const int64_t lev = one_level ? 0 : blockIdx.y;
+    const int64_t nvar = a.nslices / a.nz;
+    const int64_t ngroups = one_level ? (a.nslices + B - 1) / B : (nvar + B - 1) / B;
     const int64_t lvl_lines = lev * a.nlines;
 
     // boundary maps of the R lines
@@ -302,13 +359,15 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     const float4 *cg = a.coef + ((lvl_lines + min(myline, a.nlines - 1)) * C) * 32 + lane;
     const double *ml = ms + warp * mre * 9;
     uint64_t rebits = 0;
-    int rank0 = 0, nre = 0;
+    int rank0 = 0, nre = 0, line_re = 0;
     float Pc[M], Pa[M];
     if (active) {
         const LaneInfo li = a.lanes[(lvl_lines + myline) * 32 + lane];
         rebits = li.rebits;
         rank0 = li.rank0;
         nre = li.nre;
+        if (mre > 0)
+            line_re = (int)(a.tail_base[lvl_lines + myline + 1] - a.tail_base[lvl_lines + myline]);
         const float *x = a.xfer + ((lvl_lines + myline) * 32 + lane) * XS;
         const int oc = ADJ ? 2 : 0, oa = ADJ ? 3 : 1;
 #pragma unroll
@@ -317,74 +376,102 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
             Pa[k] = x[oa * M + k];
         }
     }
-    float *dl[B], *yl[B];
+    // data layout: lane value u of line r at T-index (u*R + r)*ss + k, i.e.
+    // slice b of line r, point k at float index W*((b/W*R + r)*ss + k) + b%W
+    T *dt = reinterpret_cast<T *>(ds);
+    T *dl[U];
+    float *yl[B];
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-        dl[b] = ds + (b * R + warp) * ss + ka;
-        yl[b] = ys + (b * R + warp) * mre * 3;
-    }
-    // load/store mapping: the x pass copies rows (16-byte pieces when
-    // aligned), the y pass copies R-column strips, thread t owning column
-    // r = t % R and rows t / R + 32 m
+    for (int u = 0; u < U; ++u) dl[u] = dt + (u * R + warp) * ss + ka;
+#pragma unroll
+    for (int b = 0; b < B; ++b) yl[b] = ys + (b * R + warp) * mre * 3;
+    // load/store mapping: the x pass copies rows, the y pass R-column
+    // strips, thread t owning column r = t % R and rows t / R + 32 m
     const int yr = threadIdx.x % R, yk0 = threadIdx.x / R;
     const int64_t row_step = 32 * a.pt_stride;
     const bool maps = mre > 0;
+    const bool vec = W == 1 && a.vec4;
 
-    for (int64_t i0 = 0; i0 < s_count; i0 += B) {
-        const int nb = (int)min((int64_t)B, s_count - i0);
+    for (int64_t gi = one_level ? blockIdx.y : 0; gi < ngroups; gi += one_level ? gridDim.y : 1) {
+        const int64_t s0 = one_level ? gi * B : gi * B * a.nz + lev;
+        const int64_t s_step = one_level ? 1 : a.nz;
+        const int nb = (int)min((int64_t)B, one_level ? a.nslices - gi * B : nvar - gi * B);
         // ---- load the lines of nb slices into shared memory
         for (int b = 0; b < nb; ++b) {
-            const float *src = a.in + (s_first + (i0 + b) * s_step) * a.plane;
-            float *db = ds + b * R * ss;
+            const float *src = a.in + (s0 + b * s_step) * a.plane;
+            float *db = ds + (b / W) * W * R * ss + b % W;
             if (a.pt_stride == 1) {
                 for (int r = 0; r < lines_here; ++r) {
                     const float *g = src + (line0 + r) * a.line_stride;
-                    float *s = db + r * ss;
-                    if (a.vec4) {
+                    float *s = db + W * r * ss;
+                    if (vec) {
                         for (int q = threadIdx.x; q < n / 4; q += blockDim.x)
                             cp_async16(s + 4 * q, g + 4 * q);
                     } else {
-                        for (int k = threadIdx.x; k < n; k += blockDim.x) cp_async4(s + k, g + k);
+                        for (int k = threadIdx.x; k < n; k += blockDim.x) cp_async4(s + W * k, g + k);
                     }
                 }
             } else if (yr < lines_here) {
                 const float *g = src + (line0 + yr) + (int64_t)yk0 * a.pt_stride;
-                float *s = db + yr * ss;
-                for (int k = yk0; k < n; k += 32, g += row_step) cp_async4(s + k, g);
+                float *s = db + W * yr * ss;
+                for (int k = yk0; k < n; k += 32, g += row_step) cp_async4(s + W * k, g);
             }
         }
         cp_async_wait_all();
         __syncthreads();
         if (active) {
             for (int it = 0; it < a.iters; ++it) {
-                float st[B][3], v[B][3], P[M];
-                // ---- A: causal, zero start -> chunk end state (land input ignored)
+                T st[U][3];
+                float v[B][3], P[M];
+                // ---- A: causal, zero start -> chunk end state (land input zeroed)
 #pragma unroll
-                for (int b = 0; b < B; ++b) st[b][0] = st[b][1] = st[b][2] = 0.f;
+                for (int u = 0; u < U; ++u) st[u][0] = st[u][1] = st[u][2] = L::zero();
                 sweep<ORDER, ADJ, B, true, true, false, false>(cg, dl, len, 0, ml, yl, 0, st);
 #pragma unroll
-                for (int b = 0; b < B; ++b) v[b][0] = st[b][0], v[b][1] = st[b][1], v[b][2] = st[b][2];
+                for (int b = 0; b < B; ++b)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) v[b][q] = L::get(st[b / W][q], b % W);
 #pragma unroll
                 for (int k = 0; k < M; ++k) P[k] = Pc[k];
                 warp_scan<ORDER, false, B>(P, v, lane);
                 // ---- B: causal from the true entering state, in place
 #pragma unroll
-                for (int b = 0; b < B; ++b) st[b][0] = v[b][0], st[b][1] = v[b][1], st[b][2] = v[b][2];
-                if (maps) sweep<ORDER, ADJ, B, true, true, true, true>(cg, dl, len, rebits, ml, yl, rank0, st);
-                else sweep<ORDER, ADJ, B, true, true, true, false>(cg, dl, len, rebits, ml, yl, rank0, st);
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        float w[W];
+#pragma unroll
+                        for (int h = 0; h < W; ++h) w[h] = v[u * W + h][q];
+                        st[u][q] = L::make(w);
+                    }
+                if (maps) {
+                    sweep<ORDER, ADJ, B, true, false, true, true>(cg, dl, len, rebits, ml, yl, rank0, st);
+                    apply_line_tails<ORDER, ADJ, B>(ml, yl, line_re, lane);
+                } else {
+                    sweep<ORDER, ADJ, B, true, false, true, false>(cg, dl, len, rebits, ml, yl, rank0, st);
+                }
                 // ---- C: anticausal from zero at the chunk end
 #pragma unroll
-                for (int b = 0; b < B; ++b) st[b][0] = st[b][1] = st[b][2] = 0.f;
+                for (int u = 0; u < U; ++u) st[u][0] = st[u][1] = st[u][2] = L::zero();
                 if (maps) sweep<ORDER, ADJ, B, false, false, false, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
                 else sweep<ORDER, ADJ, B, false, false, false, false>(cg, dl, len, rebits, ml, yl, 0, st);
 #pragma unroll
-                for (int b = 0; b < B; ++b) v[b][0] = st[b][0], v[b][1] = st[b][1], v[b][2] = st[b][2];
+                for (int b = 0; b < B; ++b)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) v[b][q] = L::get(st[b / W][q], b % W);
 #pragma unroll
                 for (int k = 0; k < M; ++k) P[k] = Pa[k];
                 warp_scan<ORDER, true, B>(P, v, lane);
                 // ---- D: anticausal from the true entering state, in place
 #pragma unroll
-                for (int b = 0; b < B; ++b) st[b][0] = v[b][0], st[b][1] = v[b][1], st[b][2] = v[b][2];
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        float w[W];
+#pragma unroll
+                        for (int h = 0; h < W; ++h) w[h] = v[u * W + h][q];
+                        st[u][q] = L::make(w);
+                    }
                 if (maps) sweep<ORDER, ADJ, B, false, false, true, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
                 else sweep<ORDER, ADJ, B, false, false, true, false>(cg, dl, len, rebits, ml, yl, 0, st);
                 __syncwarp();
@@ -393,23 +480,23 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
         __syncthreads();
         // ---- store
         for (int b = 0; b < nb; ++b) {
-            float *dst = a.out + (s_first + (i0 + b) * s_step) * a.plane;
-            const float *db = ds + b * R * ss;
+            float *dst = a.out + (s0 + b * s_step) * a.plane;
+            const float *db = ds + (b / W) * W * R * ss + b % W;
             if (a.pt_stride == 1) {
                 for (int r = 0; r < lines_here; ++r) {
                     float *g = dst + (line0 + r) * a.line_stride;
-                    const float *s = db + r * ss;
-                    if (a.vec4) {
+                    const float *s = db + W * r * ss;
+                    if (vec) {
                         for (int q = threadIdx.x; q < n / 4; q += blockDim.x)
                             reinterpret_cast<float4 *>(g)[q] = reinterpret_cast<const float4 *>(s)[q];
                     } else {
-                        for (int k = threadIdx.x; k < n; k += blockDim.x) g[k] = s[k];
+                        for (int k = threadIdx.x; k < n; k += blockDim.x) g[k] = s[W * k];
                     }
                 }
             } else if (yr < lines_here) {
                 float *g = dst + (line0 + yr) + (int64_t)yk0 * a.pt_stride;
-                const float *s = db + yr * ss;
-                for (int k = yk0; k < n; k += 32, g += row_step) *g = s[k];
+                const float *s = db + W * yr * ss;
+                for (int k = yk0; k < n; k += 32, g += row_step) *g = s[W * k];
             }
         }
         __syncthreads();   // stores read ds before the next slices' copies land
