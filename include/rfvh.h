@@ -133,6 +133,16 @@ rf_status rf_apply_adjoint(rf_plan p, const float *const *in,
 rf_status rf_apply_host(rf_plan p, const float *const *in, float *const *out,
                         int nvar, int adjoint, void *stream);
 
+/* Launch-shape autotuner.  For `nvar` variables per domain, times every
+ * shape the tile kernel is built for (lines per CTA, slices per thread,
+ * single or double buffering) that fits shared memory, for the forward and
+ * the adjoint operator in each direction of each domain, on plan-owned
+ * scratch fields (allocated for the call and freed before it returns), and
+ * keeps the fastest for later rf_apply / rf_apply_adjoint calls with the same
+ * nvar.  Without tuning a fixed rule picks the shape.  Synchronises `stream`.
+ * Errors: RF_EINVAL (null plan, nvar < 1), RF_ENOMEM, RF_ECUDA. */
+rf_status rf_plan_tune(rf_plan p, int nvar, void *stream);
+
 /* Sticky status of the plan: RF_OK, or the first error a launch or a
  * device-side check recorded since the plan was built. */
 rf_status rf_plan_status(rf_plan p);

@@ -25,6 +25,27 @@ struct TailSpec {
     int n_img;
 };
 
+// (lines per CTA, slices per thread) of a tile-kernel launch.
+struct TileShape {
+    int R, B;
+};
+
+// How one direction of one domain is launched for a given slice count.
+struct LaunchCfg {
+    bool tile = false;     // tile kernel (else the long-line kernel)
+    TileShape sh{0, 0};
+    size_t smem = 0;
+    int occ = 0;           // resident CTAs per SM
+    int nbuf = 1;          // data buffers in shared memory (1 or 2)
+    int64_t groups = 1;    // CTA rows along the slices
+};
+
+struct CfgEntry {
+    int64_t nslices;
+    bool adjoint;
+    LaunchCfg cfg;
+};
+
 // Everything one direction (x: rows, y: columns) of one domain needs.
 struct Dir {
     int64_t n = 0, nlines = 0;       // line length, lines per slice
@@ -41,6 +62,7 @@ struct Dir {
     LaneInfo *lanes = nullptr;       // [ncl][nlines][32]
     int64_t ntail = 0;
     int max_re = 0;                  // most segment ends on one line
+    std::vector<CfgEntry> cfgs;      // launch shapes chosen so far
 };
 
 struct Domain {
@@ -346,35 +368,10 @@ void choose_chunk(Dir &q)
 
 // (lines per CTA, slices per thread) pairs the tile kernel is built for, in
 // order of preference.
-struct TileShape {
-    int R, B;
-};
 constexpr TileShape kShapesY[] = {{8, 4}, {8, 2}, {4, 4}, {8, 1}, {4, 2}, {2, 4},
                                   {4, 1}, {2, 1}, {1, 4}, {1, 1}};
 constexpr TileShape kShapesX[] = {{4, 4}, {8, 4}, {2, 4}, {4, 2}, {8, 2}, {4, 1},
                                   {8, 1}, {1, 4}, {2, 1}, {1, 1}};
-
-// Pick the tile shape for one launch: the first shape whose shared memory
-// allows two CTAs per SM (else one), with B no larger than the slices a CTA
-// gets.  Returns false if even one line of one slice does not fit.
-bool pick_shape(const Dir &q, bool along_y, int64_t slices_per_cta, TileShape &sh,
-                size_t &smem)
-{
-    const int64_t ss = smem_stride(q.n);
-    for (int pass = 0; pass < 2; ++pass) {
-        const size_t cap = pass == 0 ? kSmemTarget : kSmemMax;
-        for (const TileShape &s : along_y ? kShapesY : kShapesX) {
-            if (s.B > 1 && s.B > slices_per_cta) continue;
-            const size_t bytes = (size_t)tile_smem_bytes(s.R, s.B, ss, q.max_re);
-            if (bytes <= cap) {
-                sh = s;
-                smem = bytes;
-                return true;
-            }
-        }
-    }
-    return false;
-}
 
 rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
                     const float *L_dev, const std::vector<int32_t> &base,
@@ -501,36 +498,117 @@ void launch_shape(const TileArgs &a, TileShape sh, int64_t nlines, int64_t group
 }
 
 // How one direction of one domain is launched for a given slice count.
-struct LaunchCfg {
-    bool tile = false;     // tile kernel (else the long-line kernel)
-    TileShape sh{0, 0};
-    size_t smem = 0;
-    int64_t groups = 1;    // CTA rows along the slices
-};
 
 // Tile shape: a CTA's slices are the variables of one level when the
 // coefficients differ per level, else the slices are split for about two
 // waves of CTAs.
-LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nslices)
+template <int ORDER, bool ADJ, int R, int B>
+int tile_occupancy(size_t smem)
 {
-    LaunchCfg L;
-    if (q.R == 0) return L;
-    const bool along_y = q.pt_stride != 1;
+    cudaFuncSetAttribute(tile_kernel<ORDER, ADJ, R, B>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_kernel<ORDER, ADJ, R, B>,
+                                                      32 * R, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return blocks;
+}
+
+template <int ORDER, bool ADJ>
+int shape_occupancy(TileShape sh, size_t smem)
+{
+#define RF_SHAPE(r, b) \
+    if (sh.R == r && sh.B == b) return tile_occupancy<ORDER, ADJ, r, b>(smem);
+    RF_SHAPE(8, 4) RF_SHAPE(8, 2) RF_SHAPE(8, 1) RF_SHAPE(4, 4) RF_SHAPE(4, 2)
+    RF_SHAPE(4, 1) RF_SHAPE(2, 4) RF_SHAPE(2, 1) RF_SHAPE(1, 4) RF_SHAPE(1, 1)
+#undef RF_SHAPE
+    return 0;
+}
+
+int num_sms()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 1;
+        }
+    }
+    return sms;
+}
+
+// Complete a launch configuration whose shape and buffer count are set:
+// shared memory, resident CTAs per SM, and the CTA rows along the slices
+// (about two waves of CTAs; one row per level when the coefficients differ
+// per level).  False if the shape does not fit or the slices per CTA are
+// fewer than B.
+template <int ORDER, bool ADJ>
+bool finish_cfg(const Domain &D, const Dir &q, int64_t nslices, LaunchCfg &L)
+{
+    const int64_t per_cta = D.ncl > 1 ? nslices / D.g.nz : nslices;
+    if (q.R == 0 || (L.sh.B > 1 && L.sh.B > per_cta)) return false;
+    L.smem = (size_t)tile_smem_bytes(L.sh.R, L.sh.B, smem_stride(q.n), q.max_re, L.nbuf);
+    if (L.smem > kSmemMax) return false;
+    L.occ = shape_occupancy<ORDER, ADJ>(L.sh, L.smem);
+    if (L.occ < 1) return false;
+    L.tile = true;
     if (D.ncl > 1) {
         L.groups = D.g.nz;
-        L.tile = pick_shape(q, along_y, nslices / D.g.nz, L.sh, L.smem);
-        return L;
-    }
-    L.tile = pick_shape(q, along_y, std::max<int64_t>(1, nslices / 8), L.sh, L.smem);
-    if (L.tile) {
+    } else {
         const int64_t gx = (q.nlines + L.sh.R - 1) / L.sh.R;
-        const int64_t per_sm = L.smem <= kSmemTarget ? 2 : 1;
-        const int64_t target = 2 * 152 * per_sm;
+        const int64_t target = 2 * (int64_t)num_sms() * L.occ;
         int64_t groups = (target + gx - 1) / gx;
         groups = std::min<int64_t>(groups, (nslices + L.sh.B - 1) / L.sh.B);
         L.groups = std::max<int64_t>(1, std::min<int64_t>(groups, 65535));
     }
-    return L;
+    return true;
+}
+
+// Default (untuned) tile shape: the first shape in the direction's
+// preference list whose single-buffered shared memory allows two CTAs per
+// SM, else the first that fits at all; the long-line kernel if none does.
+template <int ORDER, bool ADJ>
+LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nslices)
+{
+    const int64_t ss = smem_stride(q.n);
+    for (int pass = 0; pass < 2; ++pass) {
+        const size_t cap = pass == 0 ? kSmemTarget : kSmemMax;
+        for (const TileShape &s : q.pt_stride != 1 ? kShapesY : kShapesX) {
+            if ((size_t)tile_smem_bytes(s.R, s.B, ss, q.max_re, 1) > cap) continue;
+            LaunchCfg L;
+            L.sh = s;
+            L.nbuf = 1;
+            if (finish_cfg<ORDER, ADJ>(D, q, nslices, L)) return L;
+        }
+    }
+    return LaunchCfg{};
+}
+
+// Every tile configuration (shape and buffer count) that fits, for tuning.
+template <int ORDER, bool ADJ>
+std::vector<LaunchCfg> launch_candidates(const Domain &D, const Dir &q, int64_t nslices)
+{
+    std::vector<LaunchCfg> out;
+    for (const TileShape &s : kShapesY)
+        for (int nbuf = 1; nbuf <= 2; ++nbuf) {
+            LaunchCfg L;
+            L.sh = s;
+            L.nbuf = nbuf;
+            if (finish_cfg<ORDER, ADJ>(D, q, nslices, L)) out.push_back(L);
+        }
+    return out;
+}
+
+LaunchCfg launch_cfg_for(const rf_plan_ *p, const Domain &D, const Dir &q, int64_t nslices,
+                         bool adjoint)
+{
+    if (p->opt.order == 3)
+        return adjoint ? launch_cfg<3, true>(D, q, nslices) : launch_cfg<3, false>(D, q, nslices);
+    return adjoint ? launch_cfg<1, true>(D, q, nslices) : launch_cfg<1, false>(D, q, nslices);
 }
 
 template <int ORDER, bool ADJ>
@@ -564,6 +642,7 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
         a.max_re = q.ntail > 0 ? q.max_re : 0;
         a.vec4 = q.pt_stride == 1 && q.n % 4 == 0 && ((uintptr_t)in % 16) == 0 &&
                  ((uintptr_t)out % 16) == 0;
+        a.nbuf = L.nbuf;
         launch_shape<ORDER, ADJ>(a, sh, q.nlines, groups, smem, st);
     } else {
         LineArgs a{};
@@ -597,7 +676,20 @@ rf_status apply_impl(rf_plan p, const float *const *in, float *const *out, int n
     for (size_t d = 0; d < p->dom.size(); ++d) {
         Domain &D = p->dom[d];
         const int64_t nslices = (int64_t)nvar * D.g.nz;
-        const LaunchCfg cfg[2] = {launch_cfg(D, D.d[0], nslices), launch_cfg(D, D.d[1], nslices)};
+        LaunchCfg cfg[2];
+        for (int dir = 0; dir < 2; ++dir) {
+            Dir &q = D.d[dir];
+            bool found = false;
+            for (const CfgEntry &e : q.cfgs)
+                if (e.nslices == nslices && e.adjoint == adjoint) {
+                    cfg[dir] = e.cfg;
+                    found = true;
+                }
+            if (!found) {
+                cfg[dir] = launch_cfg_for(p, D, q, nslices, adjoint);
+                q.cfgs.push_back({nslices, adjoint, cfg[dir]});
+            }
+        }
         // global scratch for segment-end states, only for the long-line path
         int64_t nt = 0;
         for (int dir = 0; dir < 2; ++dir)
@@ -626,6 +718,92 @@ rf_status apply_impl(rf_plan p, const float *const *in, float *const *out, int n
         }
     }
     return RF_OK;
+}
+
+// One launch of direction q with configuration L, for tuning.
+void launch_any(const rf_plan_ *p, const Domain &D, const Dir &q, const LaunchCfg &L,
+                const float *in, float *out, int64_t nslices, bool adjoint, cudaStream_t st)
+{
+    const int K = p->opt.iters;
+    if (p->opt.order == 3) {
+        if (adjoint) launch_dir<3, true>(D, q, L, in, out, nslices, 1, st);
+        else launch_dir<3, false>(D, q, L, in, out, nslices, 1, st);
+    } else {
+        if (adjoint) launch_dir<1, true>(D, q, L, in, out, nslices, K, st);
+        else launch_dir<1, false>(D, q, L, in, out, nslices, K, st);
+    }
+}
+
+std::vector<LaunchCfg> candidates_for(const rf_plan_ *p, const Domain &D, const Dir &q,
+                                      int64_t nslices, bool adjoint)
+{
+    if (p->opt.order == 3)
+        return adjoint ? launch_candidates<3, true>(D, q, nslices)
+                       : launch_candidates<3, false>(D, q, nslices);
+    return adjoint ? launch_candidates<1, true>(D, q, nslices)
+                   : launch_candidates<1, false>(D, q, nslices);
+}
+
+// Autotuner: time every candidate configuration of every direction of every
+// domain on scratch fields (zeros; the work does not depend on the values)
+// and remember the fastest.
+rf_status tune_impl(rf_plan_ *p, int nvar, cudaStream_t st)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return RF_ECUDA;
+    }
+    rf_status s = RF_OK;
+    for (Domain &D : p->dom) {
+        const int64_t nslices = (int64_t)nvar * D.g.nz;
+        const int64_t nf = nslices * D.g.nx * D.g.ny;
+        float *buf = nullptr;
+        int64_t dummy = 0;
+        s = dev_alloc(&buf, 2 * nf, &dummy);
+        if (s != RF_OK) break;
+        s = cuda_status(cudaMemsetAsync(buf, 0, sizeof(float) * 2 * (size_t)nf, st));
+        for (int adj = 0; adj < 2 && s == RF_OK; ++adj) {
+            for (int dir = 0; dir < 2 && s == RF_OK; ++dir) {
+                Dir &q = D.d[dir];
+                const std::vector<LaunchCfg> cands = candidates_for(p, D, q, nslices, adj != 0);
+                if (cands.empty()) continue;
+                float best_ms = 0.f;
+                LaunchCfg best;
+                for (const LaunchCfg &L : cands) {
+                    launch_any(p, D, q, L, buf, buf + nf, nslices, adj != 0, st);   // warm-up
+                    cudaEventRecord(e0, st);
+                    for (int r = 0; r < 3; ++r)
+                        launch_any(p, D, q, L, buf, buf + nf, nslices, adj != 0, st);
+                    cudaEventRecord(e1, st);
+                    s = cuda_status(cudaEventSynchronize(e1));
+                    if (s != RF_OK) break;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (best_ms == 0.f || ms < best_ms) {
+                        best_ms = ms;
+                        best = L;
+                    }
+                }
+                if (s != RF_OK) break;
+                bool found = false;
+                for (CfgEntry &e : q.cfgs)
+                    if (e.nslices == nslices && e.adjoint == (adj != 0)) {
+                        e.cfg = best;
+                        found = true;
+                    }
+                if (!found) q.cfgs.push_back({nslices, adj != 0, best});
+            }
+        }
+        cudaStreamSynchronize(st);
+        cudaFree(buf);
+        if (s != RF_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == RF_OK) s = cuda_status(cudaGetLastError());
+    return s;
 }
 
 }  // namespace
@@ -711,6 +889,12 @@ rf_status rf_apply_host(rf_plan p, const float *const *in, float *const *out,
                                            cudaMemcpyDeviceToHost, st)));
     }
     return cuda_status(cudaStreamSynchronize(st));
+}
+
+rf_status rf_plan_tune(rf_plan p, int nvar, void *stream)
+{
+    if (!p || nvar < 1) return RF_EINVAL;
+    return tune_impl(p, nvar, (cudaStream_t)stream);
 }
 
 rf_status rf_plan_status(rf_plan p)

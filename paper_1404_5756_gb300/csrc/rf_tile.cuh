@@ -58,6 +58,7 @@ struct TileArgs {
     int smem_stride;          // floats per line row in shared memory
     int max_re;               // boundary-map slots per line (0: no maps)
     int vec4;                 // rows 16-byte aligned (x pass)
+    int nbuf;                 // data buffers: 1 or 2 (copies overlap filtering)
 };
 
 constexpr int kMaxChunk = 64;
@@ -173,15 +174,15 @@ __device__ __forceinline__ void warp_scan(float *P, float (*v)[3], int lane)
 }
 
 // Shared-memory bytes of the tile kernel.  Layout: 16-byte guard | maps
-// [R][max_re][9] double (padded to 16 bytes) | data [B/W][R][ss] units of W
-// slices | starts [B][R][max_re][3] float | 16-byte guard.  The guards keep
-// the sweeps' one-step-ahead data prefetch (one element past either end of a
-// chunk) inside the allocation.
+// [R][max_re][9] double (padded to 16 bytes) | nbuf data buffers (1 or 2),
+// each [B/W][R][ss] units of W slices | starts [B][R][max_re][3] float |
+// 16-byte guard.  The guards keep the sweeps' one-step-ahead data prefetch
+// (one element past either end of a chunk) inside the allocation.
 __host__ __device__ inline int64_t tile_smem_bytes(int64_t R, int64_t B, int64_t ss,
-                                                   int64_t max_re)
+                                                   int64_t max_re, int64_t nbuf)
 {
     const int64_t maps = (R * max_re * 9 + 1) / 2 * 2;
-    return 16 + maps * 8 + B * R * ss * 4 + B * R * max_re * 12 + 16;
+    return 16 + maps * 8 + nbuf * B * R * ss * 4 + B * R * max_re * 12 + 16;
 }
 
 // B slices per thread travel as U = B/W lane values of W slices each: pairs
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     const int n = (int)a.n, C = a.C, ss = a.smem_stride, mre = a.max_re;
     double *ms = reinterpret_cast<double *>(smem_raw + 16);
     float *ds = reinterpret_cast<float *>(ms + ((R * mre * 9 + 1) & ~1));
-    float *ys = ds + B * R * ss;
+    float *ys = ds + a.nbuf * B * R * ss;   // after the data buffers
     const int64_t line0 = (int64_t)blockIdx.x * R;
     const int64_t myline = line0 + warp;
     const bool active = myline < a.nlines;
@@ -382,8 +383,6 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     T *dl[U];
     float *yl[B];
 #pragma unroll
-    for (int u = 0; u < U; ++u) dl[u] = dt + (u * R + warp) * ss + ka;
-#pragma unroll
     for (int b = 0; b < B; ++b) yl[b] = ys + (b * R + warp) * mre * 3;
     // load/store mapping: the x pass copies rows, the y pass R-column
     // strips, thread t owning column r = t % R and rows t / R + 32 m
@@ -392,14 +391,21 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     const bool maps = mre > 0;
     const bool vec = W == 1 && a.vec4;
 
-    for (int64_t gi = one_level ? blockIdx.y : 0; gi < ngroups; gi += one_level ? gridDim.y : 1) {
-        const int64_t s0 = one_level ? gi * B : gi * B * a.nz + lev;
-        const int64_t s_step = one_level ? 1 : a.nz;
-        const int nb = (int)min((int64_t)B, one_level ? a.nslices - gi * B : nvar - gi * B);
-        // ---- load the lines of nb slices into shared memory
+    // Slice groups of this CTA, double buffered: the copies of the next
+    // group are in flight while the current one is filtered.
+    const int64_t g_first = one_level ? blockIdx.y : 0;
+    const int64_t g_step = one_level ? gridDim.y : 1;
+    const int64_t s_step = one_level ? 1 : a.nz;
+    auto group_first = [&](int64_t gi) { return one_level ? gi * B : gi * B * a.nz + lev; };
+    auto group_size = [&](int64_t gi) {
+        return (int)min((int64_t)B, one_level ? a.nslices - gi * B : nvar - gi * B);
+    };
+    auto issue_loads = [&](int64_t gi, int buf) {
+        const int64_t s0 = group_first(gi);
+        const int nb = group_size(gi);
         for (int b = 0; b < nb; ++b) {
             const float *src = a.in + (s0 + b * s_step) * a.plane;
-            float *db = ds + (b / W) * W * R * ss + b % W;
+            float *db = ds + (int64_t)buf * B * R * ss + (b / W) * W * R * ss + b % W;
             if (a.pt_stride == 1) {
                 for (int r = 0; r < lines_here; ++r) {
                     const float *g = src + (line0 + r) * a.line_stride;
@@ -417,8 +423,22 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
                 for (int k = yk0; k < n; k += 32, g += row_step) cp_async4(s + W * k, g);
             }
         }
-        cp_async_wait_all();
-        __syncthreads();
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+    // one buffer: copy, filter, store in turn; two: the next group's copies
+    // fly while the current group is filtered
+    const bool dbl = a.nbuf == 2;
+    if (dbl && g_first < ngroups) issue_loads(g_first, 0);
+    int buf = 0;
+    for (int64_t gi = g_first; gi < ngroups; gi += g_step, buf ^= (dbl ? 1 : 0)) {
+        const int64_t s0 = group_first(gi);
+        const int nb = group_size(gi);
+        if (!dbl) issue_loads(gi, 0);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();   // group gi has landed; the other buffer is free
+        if (dbl && gi + g_step < ngroups) issue_loads(gi + g_step, buf ^ 1);
+#pragma unroll
+        for (int u = 0; u < U; ++u) dl[u] = dt + ((int64_t)buf * U * R + u * R + warp) * ss + ka;
         if (active) {
             for (int it = 0; it < a.iters; ++it) {
                 T st[U][3];
@@ -481,7 +501,7 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
         // ---- store
         for (int b = 0; b < nb; ++b) {
             float *dst = a.out + (s0 + b * s_step) * a.plane;
-            const float *db = ds + (b / W) * W * R * ss + b % W;
+            const float *db = ds + (int64_t)buf * B * R * ss + (b / W) * W * R * ss + b % W;
             if (a.pt_stride == 1) {
                 for (int r = 0; r < lines_here; ++r) {
                     float *g = dst + (line0 + r) * a.line_stride;
@@ -499,8 +519,9 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
                 for (int k = yk0; k < n; k += 32, g += row_step) *g = s[W * k];
             }
         }
-        __syncthreads();   // stores read ds before the next slices' copies land
+        if (!dbl) __syncthreads();   // stores read the buffer the next copies fill
     }
+    cp_async_wait_all();   // a CTA without slices still owns its map copies
 }
 
 }  // namespace rfvh

@@ -92,6 +92,12 @@ class Plan:
         """(points per variable, domains, device bytes owned, kernel launches)."""
         return _lib.rf_plan_info(self._plan)
 
+    def tune(self, nvar: int) -> None:
+        """Time the tile-kernel launch shapes for `nvar` variables and keep the
+        fastest (rf_plan_tune); synchronises the current stream."""
+        with torch.cuda.device(self.device):
+            _lib.rf_plan_tune(self._plan, nvar, _stream_handle(self.device))
+
     def status(self) -> int:
         return _lib.rf_plan_status(self._plan)
 

@@ -17,7 +17,7 @@ def test_header_declares_the_boundary():
     names = _lib.declared_functions()
     for n in ["rf_coeffs", "rf_apply", "rf_apply_adjoint", "rf_plan_status",
               "rf_plan_destroy", "rf_status_string", "rf_options_default",
-              "rf_apply_host", "rf_plan_info"]:
+              "rf_apply_host", "rf_plan_info", "rf_plan_tune"]:
         assert n in names
 
 
@@ -78,6 +78,7 @@ def test_apply_rejects_bad_arguments(lib):
     assert lib.rf_apply_adjoint(None, arr, arr, 1, None) == E
     assert lib.rf_apply_host(None, arr, arr, 1, 0, None) == E
     assert lib.rf_plan_status(None) == E
+    assert lib.rf_plan_tune(None, 1, None) == E
     assert lib.rf_plan_info(None, None, None, None, None) == E
     assert lib.rf_plan_destroy(None) == _lib.RF_OK
 

@@ -223,3 +223,32 @@ def test_autograd_backward_is_adjoint_and_matches_finite_differences():
         fd = (J(v + d).double() - J(v - d).double()) / 2.0
     an = (v.grad.double() * d.double()).sum()
     assert abs(fd.item() - an.item()) <= 1e-4 * abs(an.item())
+
+
+def test_tuned_shapes_give_identical_results():
+    """The autotuner only changes lines per CTA, slices per thread and
+    buffering, never the arithmetic of a slice: results are bit-identical."""
+    w = synth.workload(2, nz=3, nvar=2)
+    x = torch.from_numpy(w["x"]).cuda()
+    for order, K in FILTERS:
+        plan = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=3), Options(order=order, iters=K))
+        ref_f, ref_a = plan.apply(x), plan.apply_adjoint(x)
+        plan.tune(2)
+        assert torch.equal(plan.apply(x), ref_f)
+        assert torch.equal(plan.apply_adjoint(x), ref_a)
+        assert plan.status() == 0
+
+
+@pytest.mark.parametrize("order,K", FILTERS)
+def test_long_lines_use_the_line_kernel(order, K):
+    """Rows of 3000 points are longer than the tile kernel takes (32 chunks
+    of at most 64 points): the one-thread-per-line kernel with its global
+    scratch for the coastal start states filters them."""
+    rng = np.random.default_rng(30)
+    ny, nx = 6, 3000
+    mask = (rng.uniform(size=(ny, nx)) > 0.15).astype(np.uint8)
+    L = rng.uniform(2.0, 30.0, (ny, nx)).astype(np.float32)
+    w = dict(mask=mask, Lx=L, Ly=L)
+    x = rng.standard_normal((2, 2, ny, nx)).astype(np.float32)
+    for adjoint in (False, True):
+        assert rel_err(run_gpu(w, x, order, K, adjoint), run_oracle(w, x, order, K, adjoint)) <= TOL
