@@ -133,6 +133,30 @@ rf_status rf_apply_adjoint(rf_plan p, const float *const *in,
 rf_status rf_apply_host(rf_plan p, const float *const *in, float *const *out,
                         int nvar, int adjoint, void *stream);
 
+/* Allocation-free variant of rf_apply / rf_apply_adjoint (adjoint != 0),
+ * for callers that must not allocate device memory at the time they apply
+ * the operator: code that runs inside a framework which owns every device
+ * allocation through its own pool, code that must not trigger the implicit
+ * synchronisation of cudaMalloc/cudaFree, or real-time loops that may not
+ * allocate after start-up.  The paper has no counterpart; it is a service of
+ * this library.  It runs the one-thread-per-line kernel for both directions
+ * and keeps the per-call scratch (the anticausal start state of every
+ * segment end of every slice, 3 floats each) in one static device array of
+ * 2^21 floats (8 MiB) inside the library, which every GPU that loads the
+ * library holds until the process exits.  The call itself performs no
+ * device allocation; the plan (built earlier by rf_coeffs) must exist.
+ *   in[d], out[d], nvar, stream   as rf_apply
+ * Limit: for every domain and direction, nvar * nz * (segment ends of that
+ * direction) * 3 must not exceed 2^21, else RF_EINVAL before any launch.
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * Every call uses the same array: calls that overlap on the GPU (other
+ * streams, other threads, other plans) race and give wrong results.  Each
+ * call writes every scratch entry it reads, so no clearing is needed.
+ * Errors: RF_EINVAL, RF_ECUDA, RF_EUNSUPPORTED (device index >= 64). */
+rf_status rf_apply_static(rf_plan p, const float *const *in, float *const *out,
+                          int nvar, int adjoint, void *stream);
+
 /* Launch-shape autotuner.  For `nvar` variables per domain, times every
  * shape the tile kernel is built for (lines per CTA, slices per thread,
  * single or double buffering) that fits shared memory, for the forward and

@@ -69,6 +69,7 @@ def load(build_if_missing: bool = False):
     lib.rf_apply.argtypes = [vp, pp, pp, i, vp]
     lib.rf_apply_adjoint.argtypes = [vp, pp, pp, i, vp]
     lib.rf_apply_host.argtypes = [vp, pp, pp, i, i, vp]
+    lib.rf_apply_static.argtypes = [vp, pp, pp, i, i, vp]
     lib.rf_plan_tune.argtypes = [vp, i, vp]
     lib.rf_plan_status.argtypes = [vp]
     lib.rf_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i),
@@ -77,7 +78,8 @@ def load(build_if_missing: bool = False):
     lib.rf_status_string.argtypes = [i]
     lib.rf_status_string.restype = ctypes.c_char_p
     for name in ("rf_options_default", "rf_coeffs", "rf_apply", "rf_apply_adjoint",
-                 "rf_apply_host", "rf_plan_tune", "rf_plan_status", "rf_plan_info",
+                 "rf_apply_host", "rf_apply_static", "rf_plan_tune", "rf_plan_status",
+                 "rf_plan_info",
                  "rf_plan_destroy"):
         getattr(lib, name).restype = i
     _lib = lib

@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "rfvh.h"
@@ -889,6 +890,105 @@ rf_status rf_apply_host(rf_plan p, const float *const *in, float *const *out,
                                            cudaMemcpyDeviceToHost, st)));
     }
     return cuda_status(cudaStreamSynchronize(st));
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------
+// Allocation-free apply.  Its scratch (the anticausal start states of the
+// segment ends) lives in one file-scope device array instead of memory the
+// plan grows with cudaMalloc, so the call allocates nothing.  Every GPU that
+// loads this library holds the array until the process exits.
+namespace {
+
+constexpr int64_t kStaticScratchFloats = (int64_t)1 << 21;   // 8 MiB
+static __device__ __align__(256) float g_static_scratch[kStaticScratchFloats];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float *g_static_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in for the address).
+rf_status static_scratch(float **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return RF_ECUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return RF_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return RF_ECUDA;
+        }
+        g_static_ptr[dev] = static_cast<float *>(ptr);
+    }
+    *out = g_static_ptr[dev];
+    return RF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rf_status rf_apply_static(rf_plan p, const float *const *in, float *const *out, int nvar,
+                          int adjoint, void *stream)
+{
+    if (!p || !in || !out || nvar < 1) return RF_EINVAL;
+    for (size_t d = 0; d < p->dom.size(); ++d) {
+        if (!in[d] || !out[d]) return RF_EINVAL;
+        const int64_t nslices = (int64_t)nvar * p->dom[d].g.nz;
+        for (const Dir &q : p->dom[d].d)
+            if (q.ntail > 0 && nslices * q.ntail * 3 > kStaticScratchFloats) return RF_EINVAL;
+    }
+    float *scr = nullptr;
+    RF_TRY(static_scratch(&scr));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool adj = adjoint != 0;
+    for (size_t d = 0; d < p->dom.size(); ++d) {
+        const Domain &D = p->dom[d];
+        const int64_t nslices = (int64_t)nvar * D.g.nz;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int dir = adj ? 1 - pass : pass;   // forward x then y
+            const Dir &q = D.d[dir];
+            LineArgs a{};
+            a.in = pass == 0 ? in[d] : out[d];
+            a.out = out[d];
+            a.coef = q.coef;
+            a.tail_base = q.tail_base;
+            a.tmap = q.tmap;
+            a.tscr = scr;
+            a.n = q.n;
+            a.nlines = q.nlines;
+            a.pt_stride = q.pt_stride;
+            a.line_stride = q.line_stride;
+            a.plane = D.g.nx * D.g.ny;
+            a.nz = D.g.nz;
+            a.nslices = nslices;
+            a.ntail = q.ntail;
+            a.ncl = D.ncl;
+            a.iters = p->opt.order == 3 ? 1 : p->opt.iters;
+            const unsigned blocks = (unsigned)((q.nlines * nslices + 127) / 128);
+            if (p->opt.order == 3) {
+                if (adj) line_kernel<3, true><<<blocks, 128, 0, st>>>(a);
+                else line_kernel<3, false><<<blocks, 128, 0, st>>>(a);
+            } else {
+                if (adj) line_kernel<1, true><<<blocks, 128, 0, st>>>(a);
+                else line_kernel<1, false><<<blocks, 128, 0, st>>>(a);
+            }
+            const rf_status s = cuda_status(cudaGetLastError());
+            if (s != RF_OK) {
+                if (p->sticky == RF_OK) p->sticky = s;
+                return s;
+            }
+            ++p->launches;
+        }
+    }
+    return RF_OK;
 }
 
 rf_status rf_plan_tune(rf_plan p, int nvar, void *stream)
