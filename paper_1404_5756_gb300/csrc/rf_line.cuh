@@ -1,9 +1,9 @@
 // rf_line.cuh -- long-line path: one thread per (line, slice), sequential
 // causal then anticausal sweeps straight from global memory.  Used only for
-// lines whose tile (coefficients, boundary maps, data) does not fit in shared
-// memory; same coefficients, boundary maps and step functions as the tile
+// lines whose tile (coefficients, boundary maps, data) does not fit the tile
+// kernel; same coefficients, boundary maps and step functions as the tile
 // kernel.  The anticausal start states of the segment ends go through a
-// global scratch array indexed by boundary-map index.
+// global scratch array indexed by slice and boundary-map index.
 #pragma once
 #include <cstdint>
 
@@ -16,9 +16,11 @@ struct LineArgs {
     float *out;
     const float4 *coef;       // [ncl][nlines][n]
     const int32_t *tail_base; // [ncl*nlines + 1]
-    const double *tmap;       // [ntail][9]
-    float *tscr;              // [nslices][ntail][3]
-    int64_t n, nlines, pt_stride, line_stride, plane, nz, nslices, ntail, ncl;
+    const float2 *tmap;       // [ntail][9] hi/lo pairs
+    float *tscr;              // [nvar*nz][ntail][3]
+    int64_t n, nlines, pt_stride, line_stride, plane, ntail, ncl;
+    int64_t nz, nvar;         // levels and variables of the field
+    int64_t k0, nk;           // this launch filters levels k0 .. k0+nk-1
     int iters;
 };
 
@@ -26,8 +28,9 @@ template <int ORDER, bool ADJ>
 __global__ void __launch_bounds__(128) line_kernel(LineArgs a)
 {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= a.nlines * a.nslices) return;
-    const int64_t slice = gid / a.nlines, line = gid - slice * a.nlines;
+    if (gid >= a.nlines * a.nvar * a.nk) return;
+    const int64_t item = gid / a.nlines, line = gid - item * a.nlines;
+    const int64_t slice = (item / a.nk) * a.nz + a.k0 + item % a.nk;
     const int64_t lev = a.ncl > 1 ? slice % a.nz : 0;
     const float4 *cf = a.coef + (lev * a.nlines + line) * a.n;
     const int64_t base = a.ntail > 0 ? a.tail_base[lev * a.nlines + line] : 0;

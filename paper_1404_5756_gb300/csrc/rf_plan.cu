@@ -42,7 +42,7 @@ struct LaunchCfg {
 };
 
 struct CfgEntry {
-    int64_t nslices;
+    int64_t nvar, nk;   // variables, levels per launch
     bool adjoint;
     LaunchCfg cfg;
 };
@@ -56,7 +56,7 @@ struct Dir {
     size_t smem = 0;
     float4 *coef = nullptr;          // [ncl][nlines][n]
     int32_t *tail_base = nullptr;    // [ncl*nlines + 1] first boundary map of each line
-    double *tmap = nullptr;          // [ntail][9], consecutive along each line
+    float2 *tmap = nullptr;          // [ntail][9] hi/lo pairs, consecutive along each line
     float *xfer = nullptr;           // [ncl][nlines][32][XF]
     float4 *coef_il_base = nullptr;  // interleaved coefficients with guards
     float4 *coef_il = nullptr;       // [ncl][nlines][C][32] (tile kernel)
@@ -74,6 +74,7 @@ struct Domain {
     int64_t tscr_floats = 0;
     float *stage = nullptr;          // host-API staging
     int64_t stage_floats = 0;
+    std::vector<std::pair<int64_t, int64_t>> batch;   // tuned (nvar, levels per batch)
 };
 
 }  // namespace
@@ -184,12 +185,19 @@ __global__ void coef_lines_kernel(int64_t ncl, int64_t nx, int64_t ny, int along
     out[idx] = c;
 }
 
+// Boundary maps in FP64, stored as hi/lo FP32 pairs (hi = m rounded to
+// FP32, lo = the rest rounded to FP32) for the compensated FP32 application.
 __global__ void tail_kernel(int64_t n, const TailSpec *__restrict__ spec,
-                            double *__restrict__ tmap, int order, int K, int norm)
+                            float2 *__restrict__ tmap, int order, int K, int norm)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    tail_map_fp64((double)spec[i].sigma, spec[i].n_img, order, K, norm, tmap + 9 * i);
+    double m[9];
+    tail_map_fp64((double)spec[i].sigma, spec[i].n_img, order, K, norm, m);
+    for (int r = 0; r < 9; ++r) {
+        const float hi = (float)m[r];
+        tmap[9 * i + r] = make_float2(hi, (float)(m[r] - (double)hi));
+    }
 }
 
 // One-step matrix of the delta form with the reset factor (rf_steps.cuh),
@@ -548,9 +556,10 @@ int num_sms()
 // per level).  False if the shape does not fit or the slices per CTA are
 // fewer than B.
 template <int ORDER, bool ADJ>
-bool finish_cfg(const Domain &D, const Dir &q, int64_t nslices, LaunchCfg &L)
+bool finish_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk, LaunchCfg &L)
 {
-    const int64_t per_cta = D.ncl > 1 ? nslices / D.g.nz : nslices;
+    const int64_t nslices = nvar * nk;
+    const int64_t per_cta = D.ncl > 1 ? nvar : nslices;
     if (q.R == 0 || (L.sh.B > 1 && L.sh.B > per_cta)) return false;
     L.smem = (size_t)tile_smem_bytes(L.sh.R, L.sh.B, smem_stride(q.n), q.max_re, L.nbuf);
     if (L.smem > kSmemMax) return false;
@@ -558,7 +567,7 @@ bool finish_cfg(const Domain &D, const Dir &q, int64_t nslices, LaunchCfg &L)
     if (L.occ < 1) return false;
     L.tile = true;
     if (D.ncl > 1) {
-        L.groups = D.g.nz;
+        L.groups = nk;
     } else {
         const int64_t gx = (q.nlines + L.sh.R - 1) / L.sh.R;
         const int64_t target = 2 * (int64_t)num_sms() * L.occ;
@@ -573,7 +582,7 @@ bool finish_cfg(const Domain &D, const Dir &q, int64_t nslices, LaunchCfg &L)
 // preference list whose single-buffered shared memory allows two CTAs per
 // SM, else the first that fits at all; the long-line kernel if none does.
 template <int ORDER, bool ADJ>
-LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nslices)
+LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk)
 {
     const int64_t ss = smem_stride(q.n);
     for (int pass = 0; pass < 2; ++pass) {
@@ -583,7 +592,7 @@ LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nslices)
             LaunchCfg L;
             L.sh = s;
             L.nbuf = 1;
-            if (finish_cfg<ORDER, ADJ>(D, q, nslices, L)) return L;
+            if (finish_cfg<ORDER, ADJ>(D, q, nvar, nk, L)) return L;
         }
     }
     return LaunchCfg{};
@@ -591,7 +600,8 @@ LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nslices)
 
 // Every tile configuration (shape and buffer count) that fits, for tuning.
 template <int ORDER, bool ADJ>
-std::vector<LaunchCfg> launch_candidates(const Domain &D, const Dir &q, int64_t nslices)
+std::vector<LaunchCfg> launch_candidates(const Domain &D, const Dir &q, int64_t nvar,
+                                         int64_t nk)
 {
     std::vector<LaunchCfg> out;
     for (const TileShape &s : kShapesY)
@@ -599,22 +609,46 @@ std::vector<LaunchCfg> launch_candidates(const Domain &D, const Dir &q, int64_t 
             LaunchCfg L;
             L.sh = s;
             L.nbuf = nbuf;
-            if (finish_cfg<ORDER, ADJ>(D, q, nslices, L)) out.push_back(L);
+            if (finish_cfg<ORDER, ADJ>(D, q, nvar, nk, L)) out.push_back(L);
         }
     return out;
 }
 
-LaunchCfg launch_cfg_for(const rf_plan_ *p, const Domain &D, const Dir &q, int64_t nslices,
-                         bool adjoint)
+LaunchCfg launch_cfg_for(const rf_plan_ *p, const Domain &D, const Dir &q, int64_t nvar,
+                         int64_t nk, bool adjoint)
 {
     if (p->opt.order == 3)
-        return adjoint ? launch_cfg<3, true>(D, q, nslices) : launch_cfg<3, false>(D, q, nslices);
-    return adjoint ? launch_cfg<1, true>(D, q, nslices) : launch_cfg<1, false>(D, q, nslices);
+        return adjoint ? launch_cfg<3, true>(D, q, nvar, nk) : launch_cfg<3, false>(D, q, nvar, nk);
+    return adjoint ? launch_cfg<1, true>(D, q, nvar, nk) : launch_cfg<1, false>(D, q, nvar, nk);
+}
+
+// Levels per launch.  x and y of a batch of levels run back to back, so a
+// batch whose field fits in L2 keeps the intermediate (the x pass output,
+// read by the y pass) on chip, at the price of smaller launches.  All levels
+// in one batch unless the autotuner found a batch size that is faster.
+int64_t batch_levels(const Domain &D, int64_t nvar)
+{
+    for (const auto &e : D.batch)
+        if (e.first == nvar) return e.second;
+    return D.g.nz;
+}
+
+// Batch sizes the autotuner tries: all levels, and batches of about 96, 48
+// and 24 MB of field.
+std::vector<int64_t> batch_candidates(const Domain &D, int64_t nvar)
+{
+    const int64_t per_level = std::max<int64_t>(1, nvar * D.g.nx * D.g.ny * 4);
+    std::vector<int64_t> out{D.g.nz};
+    for (int64_t mb : {96, 48, 24}) {
+        const int64_t nk = std::max<int64_t>(1, std::min<int64_t>(D.g.nz, (mb << 20) / per_level));
+        if (std::find(out.begin(), out.end(), nk) == out.end()) out.push_back(nk);
+    }
+    return out;
 }
 
 template <int ORDER, bool ADJ>
 void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *in,
-                float *out, int64_t nslices, int iters, cudaStream_t st)
+                float *out, int64_t nvar, int64_t k0, int64_t nk, int iters, cudaStream_t st)
 {
     const int64_t plane = D.g.nx * D.g.ny;
     const TileShape sh = L.sh;
@@ -636,7 +670,9 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
         a.line_stride = q.line_stride;
         a.plane = plane;
         a.nz = D.g.nz;
-        a.nslices = nslices;
+        a.nvar = nvar;
+        a.k0 = k0;
+        a.nk = nk;
         a.ncl = D.ncl;
         a.iters = iters;
         a.smem_stride = (int)smem_stride(q.n);
@@ -659,56 +695,56 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
         a.line_stride = q.line_stride;
         a.plane = plane;
         a.nz = D.g.nz;
-        a.nslices = nslices;
+        a.nvar = nvar;
+        a.k0 = k0;
+        a.nk = nk;
         a.ntail = q.ntail;
         a.ncl = D.ncl;
         a.iters = iters;
-        const int64_t threads = q.nlines * nslices;
+        const int64_t threads = q.nlines * nvar * nk;
         line_kernel<ORDER, ADJ><<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(a);
     }
 }
 
-rf_status apply_impl(rf_plan p, const float *const *in, float *const *out, int nvar,
-                     bool adjoint, cudaStream_t st)
+// Launch configuration of direction dir for nvar variables and batches of
+// nk levels: the tuned or cached one, else the default.
+LaunchCfg cfg_of(const rf_plan_ *p, Domain &D, int dir, int64_t nvar, int64_t nk, bool adjoint)
 {
-    if (!p || !in || !out || nvar < 1) return RF_EINVAL;
-    for (size_t d = 0; d < p->dom.size(); ++d)
-        if (!in[d] || !out[d]) return RF_EINVAL;
-    for (size_t d = 0; d < p->dom.size(); ++d) {
-        Domain &D = p->dom[d];
-        const int64_t nslices = (int64_t)nvar * D.g.nz;
-        LaunchCfg cfg[2];
-        for (int dir = 0; dir < 2; ++dir) {
-            Dir &q = D.d[dir];
-            bool found = false;
-            for (const CfgEntry &e : q.cfgs)
-                if (e.nslices == nslices && e.adjoint == adjoint) {
-                    cfg[dir] = e.cfg;
-                    found = true;
-                }
-            if (!found) {
-                cfg[dir] = launch_cfg_for(p, D, q, nslices, adjoint);
-                q.cfgs.push_back({nslices, adjoint, cfg[dir]});
-            }
-        }
-        // global scratch for segment-end states, only for the long-line path
-        int64_t nt = 0;
-        for (int dir = 0; dir < 2; ++dir)
-            if (!cfg[dir].tile) nt = std::max(nt, D.d[dir].ntail);
-        rf_status s = ensure(&D.tscr, &D.tscr_floats, nslices * nt * 3, &p->bytes);
-        if (s != RF_OK) return s;
+    Dir &q = D.d[dir];
+    for (const CfgEntry &e : q.cfgs)
+        if (e.nvar == nvar && e.nk == nk && e.adjoint == adjoint) return e.cfg;
+    const LaunchCfg c = launch_cfg_for(p, D, q, nvar, nk, adjoint);
+    q.cfgs.push_back({nvar, nk, adjoint, c});
+    return c;
+}
+
+// V_H (or its adjoint) on one domain, in batches of nkb levels.
+rf_status apply_domain(rf_plan_ *p, Domain &D, const float *in, float *out, int nvar,
+                       bool adjoint, int64_t nkb, cudaStream_t st)
+{
+    const int64_t nz = D.g.nz;
+    // global scratch for segment-end states, only for the long-line path
+    int64_t nt = 0;
+    for (int dir = 0; dir < 2; ++dir)
+        if (!cfg_of(p, D, dir, nvar, nkb, adjoint).tile ||
+            !cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint).tile)
+            nt = std::max(nt, D.d[dir].ntail);
+    rf_status s = ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 3, &p->bytes);
+    if (s != RF_OK) return s;
+    const int K = p->opt.iters;
+    for (int64_t k0 = 0; k0 < nz; k0 += nkb) {
+        const int64_t nk = std::min(nkb, nz - k0);
         for (int pass = 0; pass < 2; ++pass) {
             const int dir = adjoint ? 1 - pass : pass;   // forward x then y
-            const float *src = pass == 0 ? in[d] : out[d];
+            const float *src = pass == 0 ? in : out;
             const Dir &q = D.d[dir];
-            const LaunchCfg &L = cfg[dir];
-            const int K = p->opt.iters;
+            const LaunchCfg L = cfg_of(p, D, dir, nvar, nk, adjoint);
             if (p->opt.order == 3) {
-                if (adjoint) launch_dir<3, true>(D, q, L, src, out[d], nslices, 1, st);
-                else launch_dir<3, false>(D, q, L, src, out[d], nslices, 1, st);
+                if (adjoint) launch_dir<3, true>(D, q, L, src, out, nvar, k0, nk, 1, st);
+                else launch_dir<3, false>(D, q, L, src, out, nvar, k0, nk, 1, st);
             } else {
-                if (adjoint) launch_dir<1, true>(D, q, L, src, out[d], nslices, K, st);
-                else launch_dir<1, false>(D, q, L, src, out[d], nslices, K, st);
+                if (adjoint) launch_dir<1, true>(D, q, L, src, out, nvar, k0, nk, K, st);
+                else launch_dir<1, false>(D, q, L, src, out, nvar, k0, nk, K, st);
             }
             s = cuda_status(cudaGetLastError());
             if (s != RF_OK) {
@@ -721,33 +757,121 @@ rf_status apply_impl(rf_plan p, const float *const *in, float *const *out, int n
     return RF_OK;
 }
 
+rf_status apply_impl(rf_plan p, const float *const *in, float *const *out, int nvar,
+                     bool adjoint, cudaStream_t st)
+{
+    if (!p || !in || !out || nvar < 1) return RF_EINVAL;
+    for (size_t d = 0; d < p->dom.size(); ++d)
+        if (!in[d] || !out[d]) return RF_EINVAL;
+    for (size_t d = 0; d < p->dom.size(); ++d) {
+        Domain &D = p->dom[d];
+        RF_TRY(apply_domain(p, D, in[d], out[d], nvar, adjoint, batch_levels(D, nvar), st));
+    }
+    return RF_OK;
+}
+
 // One launch of direction q with configuration L, for tuning.
 void launch_any(const rf_plan_ *p, const Domain &D, const Dir &q, const LaunchCfg &L,
-                const float *in, float *out, int64_t nslices, bool adjoint, cudaStream_t st)
+                const float *in, float *out, int64_t nvar, int64_t nk, bool adjoint,
+                cudaStream_t st)
 {
     const int K = p->opt.iters;
     if (p->opt.order == 3) {
-        if (adjoint) launch_dir<3, true>(D, q, L, in, out, nslices, 1, st);
-        else launch_dir<3, false>(D, q, L, in, out, nslices, 1, st);
+        if (adjoint) launch_dir<3, true>(D, q, L, in, out, nvar, 0, nk, 1, st);
+        else launch_dir<3, false>(D, q, L, in, out, nvar, 0, nk, 1, st);
     } else {
-        if (adjoint) launch_dir<1, true>(D, q, L, in, out, nslices, K, st);
-        else launch_dir<1, false>(D, q, L, in, out, nslices, K, st);
+        if (adjoint) launch_dir<1, true>(D, q, L, in, out, nvar, 0, nk, K, st);
+        else launch_dir<1, false>(D, q, L, in, out, nvar, 0, nk, K, st);
     }
 }
 
 std::vector<LaunchCfg> candidates_for(const rf_plan_ *p, const Domain &D, const Dir &q,
-                                      int64_t nslices, bool adjoint)
+                                      int64_t nvar, int64_t nk, bool adjoint)
 {
     if (p->opt.order == 3)
-        return adjoint ? launch_candidates<3, true>(D, q, nslices)
-                       : launch_candidates<3, false>(D, q, nslices);
-    return adjoint ? launch_candidates<1, true>(D, q, nslices)
-                   : launch_candidates<1, false>(D, q, nslices);
+        return adjoint ? launch_candidates<3, true>(D, q, nvar, nk)
+                       : launch_candidates<3, false>(D, q, nvar, nk);
+    return adjoint ? launch_candidates<1, true>(D, q, nvar, nk)
+                   : launch_candidates<1, false>(D, q, nvar, nk);
 }
 
-// Autotuner: time every candidate configuration of every direction of every
-// domain on scratch fields (zeros; the work does not depend on the values)
-// and remember the fastest.
+// Autotuner.  For every batch size of batch_candidates: time every candidate
+// launch configuration of every direction on scratch fields (zeros; the work
+// does not depend on the values) and keep the fastest, then time whole
+// forward + adjoint applications with those configurations.  The batch size
+// of the fastest application is kept.
+rf_status tune_shapes(rf_plan_ *p, Domain &D, int nvar, int64_t nk, float *buf, int64_t nf,
+                      cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st)
+{
+    for (int adj = 0; adj < 2; ++adj) {
+        for (int dir = 0; dir < 2; ++dir) {
+            Dir &q = D.d[dir];
+            const std::vector<LaunchCfg> cands = candidates_for(p, D, q, nvar, nk, adj != 0);
+            if (cands.empty()) continue;
+            float best_ms = 0.f;
+            LaunchCfg best;
+            for (const LaunchCfg &L : cands) {
+                launch_any(p, D, q, L, buf, buf + nf, nvar, nk, adj != 0, st);   // warm-up
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3; ++r)
+                    launch_any(p, D, q, L, buf, buf + nf, nvar, nk, adj != 0, st);
+                cudaEventRecord(e1, st);
+                RF_TRY(cuda_status(cudaEventSynchronize(e1)));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (best_ms == 0.f || ms < best_ms) {
+                    best_ms = ms;
+                    best = L;
+                }
+            }
+            bool found = false;
+            for (CfgEntry &e : q.cfgs)
+                if (e.nvar == nvar && e.nk == nk && e.adjoint == (adj != 0)) {
+                    e.cfg = best;
+                    found = true;
+                }
+            if (!found) q.cfgs.push_back({nvar, nk, adj != 0, best});
+        }
+    }
+    return RF_OK;
+}
+
+rf_status tune_domain(rf_plan_ *p, Domain &D, int nvar, float *buf, int64_t nf, cudaEvent_t e0,
+                      cudaEvent_t e1, cudaStream_t st)
+{
+    RF_TRY(cuda_status(cudaMemsetAsync(buf, 0, sizeof(float) * 2 * (size_t)nf, st)));
+    const int64_t nz = D.g.nz;
+    float best_ms = 0.f;
+    int64_t best_nkb = nz;
+    for (int64_t nkb : batch_candidates(D, nvar)) {
+        // a full batch and the remainder
+        RF_TRY(tune_shapes(p, D, nvar, nkb, buf, nf, e0, e1, st));
+        const int64_t rest = nz - (nz - 1) / nkb * nkb;
+        if (rest != nkb) RF_TRY(tune_shapes(p, D, nvar, rest, buf, nf, e0, e1, st));
+        for (int rep = 0; rep < 3; ++rep) {   // one warm-up, then two timed
+            if (rep == 1) cudaEventRecord(e0, st);
+            RF_TRY(apply_domain(p, D, buf, buf + nf, nvar, false, nkb, st));
+            RF_TRY(apply_domain(p, D, buf + nf, buf, nvar, true, nkb, st));
+        }
+        cudaEventRecord(e1, st);
+        RF_TRY(cuda_status(cudaEventSynchronize(e1)));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms == 0.f || ms < best_ms) {
+            best_ms = ms;
+            best_nkb = nkb;
+        }
+    }
+    bool found = false;
+    for (auto &e : D.batch)
+        if (e.first == nvar) {
+            e.second = best_nkb;
+            found = true;
+        }
+    if (!found) D.batch.push_back({nvar, best_nkb});
+    return RF_OK;
+}
+
 rf_status tune_impl(rf_plan_ *p, int nvar, cudaStream_t st)
 {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -756,51 +880,20 @@ rf_status tune_impl(rf_plan_ *p, int nvar, cudaStream_t st)
         if (e0) cudaEventDestroy(e0);
         return RF_ECUDA;
     }
+    const int64_t launches = p->launches;   // tuning launches are not counted
     rf_status s = RF_OK;
     for (Domain &D : p->dom) {
-        const int64_t nslices = (int64_t)nvar * D.g.nz;
-        const int64_t nf = nslices * D.g.nx * D.g.ny;
+        const int64_t nf = (int64_t)nvar * D.g.nz * D.g.nx * D.g.ny;
         float *buf = nullptr;
         int64_t dummy = 0;
         s = dev_alloc(&buf, 2 * nf, &dummy);
         if (s != RF_OK) break;
-        s = cuda_status(cudaMemsetAsync(buf, 0, sizeof(float) * 2 * (size_t)nf, st));
-        for (int adj = 0; adj < 2 && s == RF_OK; ++adj) {
-            for (int dir = 0; dir < 2 && s == RF_OK; ++dir) {
-                Dir &q = D.d[dir];
-                const std::vector<LaunchCfg> cands = candidates_for(p, D, q, nslices, adj != 0);
-                if (cands.empty()) continue;
-                float best_ms = 0.f;
-                LaunchCfg best;
-                for (const LaunchCfg &L : cands) {
-                    launch_any(p, D, q, L, buf, buf + nf, nslices, adj != 0, st);   // warm-up
-                    cudaEventRecord(e0, st);
-                    for (int r = 0; r < 3; ++r)
-                        launch_any(p, D, q, L, buf, buf + nf, nslices, adj != 0, st);
-                    cudaEventRecord(e1, st);
-                    s = cuda_status(cudaEventSynchronize(e1));
-                    if (s != RF_OK) break;
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (best_ms == 0.f || ms < best_ms) {
-                        best_ms = ms;
-                        best = L;
-                    }
-                }
-                if (s != RF_OK) break;
-                bool found = false;
-                for (CfgEntry &e : q.cfgs)
-                    if (e.nslices == nslices && e.adjoint == (adj != 0)) {
-                        e.cfg = best;
-                        found = true;
-                    }
-                if (!found) q.cfgs.push_back({nslices, adj != 0, best});
-            }
-        }
+        s = tune_domain(p, D, nvar, buf, nf, e0, e1, st);
         cudaStreamSynchronize(st);
         cudaFree(buf);
         if (s != RF_OK) break;
     }
+    p->launches = launches;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s == RF_OK) s = cuda_status(cudaGetLastError());
@@ -968,7 +1061,9 @@ rf_status rf_apply_static(rf_plan p, const float *const *in, float *const *out, 
             a.line_stride = q.line_stride;
             a.plane = D.g.nx * D.g.ny;
             a.nz = D.g.nz;
-            a.nslices = nslices;
+            a.nvar = nvar;
+            a.k0 = 0;
+            a.nk = D.g.nz;
             a.ntail = q.ntail;
             a.ncl = D.ncl;
             a.iters = p->opt.order == 3 ? 1 : p->opt.iters;

@@ -144,20 +144,52 @@ __device__ __forceinline__ float step(float x, const float4 &c, float *s)
     return stepv<V1, ORDER, ADJ>(x, cv, s);
 }
 
-// Coastal boundary map: forward Y = M X, adjoint Y = M^T X, in FP64.
+// Sum of three products m_k x_k, each m_k given as an unevaluated FP32 pair
+// hi + lo, by Dot2 of Ogita, Rump & Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26, 2005): the products' rounding errors (by FMA) and
+// the additions' rounding errors (by Knuth's TwoSum) are carried in a second
+// accumulator, so the result is as accurate as if it were computed in twice
+// the working precision and rounded once.  FP32 only: on this part FP64
+// issues at a small fraction of the FP32 rate.
+__device__ __forceinline__ float dot2_3(float2 m0, float2 m1, float2 m2, float x0, float x1,
+                                        float x2)
+{
+    float p = __fmul_rn(m0.x, x0);
+    float e = __fmaf_rn(m0.x, x0, -p);
+    e = __fmaf_rn(m0.y, x0, e);
+    const float2 m[2] = {m1, m2};
+    const float x[2] = {x1, x2};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float h = __fmul_rn(m[k].x, x[k]);
+        const float r = __fmaf_rn(m[k].x, x[k], -h);
+        const float s = __fadd_rn(p, h);
+        const float z = __fsub_rn(s, p);
+        const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(s, z)), __fsub_rn(h, z));
+        e = __fadd_rn(e, __fadd_rn(q, r));
+        e = __fmaf_rn(m[k].y, x[k], e);
+        p = s;
+    }
+    return __fadd_rn(p, e);
+}
+
+// Coastal boundary map: forward Y = M X, adjoint Y = M^T X.  M is stored
+// row-major as nine hi/lo FP32 pairs of the FP64 map.
 template <int ORDER, bool ADJ>
-__device__ __forceinline__ void apply_tail(const double *M, const float *X, float *Y)
+__device__ __forceinline__ void apply_tail(const float2 *M, const float *X, float *Y)
 {
     if (ORDER == 3) {
-        const double x0 = X[0], x1 = X[1], x2 = X[2];
+        const float x0 = X[0], x1 = X[1], x2 = X[2];
+        float v[3];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const double v = ADJ ? M[r] * x0 + M[3 + r] * x1 + M[6 + r] * x2
-                                 : M[3 * r] * x0 + M[3 * r + 1] * x1 + M[3 * r + 2] * x2;
-            Y[r] = (float)v;
-        }
+        for (int r = 0; r < 3; ++r)
+            v[r] = ADJ ? dot2_3(M[r], M[3 + r], M[6 + r], x0, x1, x2)
+                       : dot2_3(M[3 * r], M[3 * r + 1], M[3 * r + 2], x0, x1, x2);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) Y[r] = v[r];
     } else {
-        Y[0] = (float)(M[0] * (double)X[0]);
+        const float p = __fmul_rn(M[0].x, X[0]);
+        Y[0] = __fadd_rn(p, __fmaf_rn(M[0].y, X[0], __fmaf_rn(M[0].x, X[0], -p)));
     }
 }
 

@@ -46,12 +46,14 @@ struct TileArgs {
     const LaneInfo *lanes;    // [ncl][nlines][32]
     const float *xfer;        // [ncl][nlines][32][XF] chunk transfers
     const int32_t *tail_base; // [ncl*nlines + 1] index of each line's first boundary map
-    const double *tmap;       // [ntail][9], consecutive along each line
+    const float2 *tmap;       // [ntail][9] hi/lo pairs, consecutive along each line
     int64_t n, nlines;        // line length, lines per slice
     int64_t pt_stride;        // distance between consecutive points of a line
     int64_t line_stride;      // distance between consecutive lines
     int64_t plane;            // floats per slice
-    int64_t nz, nslices;
+    int64_t nz;               // levels of the field
+    int64_t nvar;             // variables of the field
+    int64_t k0, nk;           // this launch filters levels k0 .. k0+nk-1
     int64_t ncl;              // coefficient levels (1 or nz)
     int C;                    // chunk length (odd, <= 64)
     int iters;
@@ -174,7 +176,7 @@ __device__ __forceinline__ void warp_scan(float *P, float (*v)[3], int lane)
 }
 
 // Shared-memory bytes of the tile kernel.  Layout: 16-byte guard | maps
-// [R][max_re][9] double (padded to 16 bytes) | nbuf data buffers (1 or 2),
+// [R][max_re][9] float2 (padded to 16 bytes) | nbuf data buffers (1 or 2),
 // each [B/W][R][ss] units of W slices | starts [B][R][max_re][3] float |
 // 16-byte guard.  The guards keep the sweeps' one-step-ahead data prefetch
 // (one element past either end of a chunk) inside the allocation.
@@ -218,7 +220,7 @@ struct LaneT<2> {
 template <int ORDER, bool ADJ, int B, bool CAUSAL, bool IN_SEA, bool WRITE, bool TAILS>
 __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
                                       typename LaneT<Pack<B>::W>::L::T *const *dp, int len,
-                                      uint64_t rebits, const double *ml, float *const *ys, int rk,
+                                      uint64_t rebits, const float2 *ml, float *const *ys, int rk,
                                       typename LaneT<Pack<B>::W>::L::T (*st)[3])
 {
     constexpr int W = Pack<B>::W, U = Pack<B>::U, NS = ORDER == 3 ? 3 : 1;
@@ -296,11 +298,11 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
 // Coastal boundary maps of one line, applied by the whole warp after the
 // causal sweep: for every segment end q of the line (lanes take q = lane,
 // lane + 32, ...) and every slice b, replace the recorded causal state X at
-// ys[b] + 3q by the anticausal start state M_q X (adjoint: M_q^T X), in FP64.
-// Spreading the segment ends over the lanes keeps the FP64 work out of the
-// divergent per-point loop.
+// ys[b] + 3q by the anticausal start state M_q X (adjoint: M_q^T X).
+// Spreading the segment ends over the lanes keeps the compensated map
+// arithmetic out of the divergent per-point loop.
 template <int ORDER, bool ADJ, int B>
-__device__ __forceinline__ void apply_line_tails(const double *ml, float *const *ys, int nre_line,
+__device__ __forceinline__ void apply_line_tails(const float2 *ml, float *const *ys, int nre_line,
                                                  int lane)
 {
     constexpr int NS = ORDER == 3 ? 3 : 1;
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     using T = typename L::T;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = (int)a.n, C = a.C, ss = a.smem_stride, mre = a.max_re;
-    double *ms = reinterpret_cast<double *>(smem_raw + 16);
+    float2 *ms = reinterpret_cast<float2 *>(smem_raw + 16);
     float *ds = reinterpret_cast<float *>(ms + ((R * mre * 9 + 1) & ~1));
     float *ys = ds + a.nbuf * B * R * ss;   // after the data buffers
     const int64_t line0 = (int64_t)blockIdx.x * R;
@@ -335,14 +337,16 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     const bool active = myline < a.nlines;
     const int lines_here = (int)min((int64_t)R, a.nlines - line0);
 
-    // Slices handled by this CTA, in groups of B sharing one coefficient
-    // level.  One level for every slice: group g holds slices g*B + b and the
-    // CTA row y takes groups y, y + rows, ...  Per-level coefficients: CTA
-    // row y is level y, its groups hold the variables v0 + b of that level.
+    // A launch filters levels k0 .. k0+nk-1 of all nvar variables.  Slices are
+    // handled in groups of B sharing one coefficient level.  One level for
+    // every slice: item i of the launch is slice (i / nk)*nz + k0 + i % nk,
+    // group g holds items g*B + b, and CTA row y takes groups y, y + rows, ...
+    // Per-level coefficients: CTA row y is level k0 + y and its groups hold
+    // the variables g*B + b of that level.
     const bool one_level = a.ncl == 1;
-    const int64_t lev = one_level ? 0 : blockIdx.y;
-    const int64_t nvar = a.nslices / a.nz;
-    const int64_t ngroups = one_level ? (a.nslices + B - 1) / B : (nvar + B - 1) / B;
+    const int64_t lev = one_level ? 0 : a.k0 + blockIdx.y;
+    const int64_t nvar = a.nvar, nitems = a.nvar * a.nk;
+    const int64_t ngroups = one_level ? (nitems + B - 1) / B : (nvar + B - 1) / B;
     const int64_t lvl_lines = lev * a.nlines;
 
     // boundary maps of the R lines
@@ -350,15 +354,15 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
         for (int r = 0; r < lines_here; ++r) {
             const int64_t base = a.tail_base[lvl_lines + line0 + r];
             const int cnt = (int)(a.tail_base[lvl_lines + line0 + r + 1] - base);
-            const double *g = a.tmap + 9 * base;
-            double *s = ms + r * mre * 9;
+            const float2 *g = a.tmap + 9 * base;
+            float2 *s = ms + r * mre * 9;
             for (int q = threadIdx.x; q < cnt * 9; q += blockDim.x) cp_async8(s + q, g + q);
         }
     }
     // my chunk [ka, kb); lanes past the line's end get an empty chunk at n
     const int ka = min(lane * C, n), kb = min(ka + C, n), len = kb - ka;
     const float4 *cg = a.coef + ((lvl_lines + min(myline, a.nlines - 1)) * C) * 32 + lane;
-    const double *ml = ms + warp * mre * 9;
+    const float2 *ml = ms + warp * mre * 9;
     uint64_t rebits = 0;
     int rank0 = 0, nre = 0, line_re = 0;
     float Pc[M], Pa[M];
@@ -395,16 +399,17 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     // group are in flight while the current one is filtered.
     const int64_t g_first = one_level ? blockIdx.y : 0;
     const int64_t g_step = one_level ? gridDim.y : 1;
-    const int64_t s_step = one_level ? 1 : a.nz;
-    auto group_first = [&](int64_t gi) { return one_level ? gi * B : gi * B * a.nz + lev; };
+    auto slice_of = [&](int64_t gi, int b) -> int64_t {
+        const int64_t i = gi * B + b;
+        return one_level ? (i / a.nk) * a.nz + a.k0 + i % a.nk : i * a.nz + lev;
+    };
     auto group_size = [&](int64_t gi) {
-        return (int)min((int64_t)B, one_level ? a.nslices - gi * B : nvar - gi * B);
+        return (int)min((int64_t)B, one_level ? nitems - gi * B : nvar - gi * B);
     };
     auto issue_loads = [&](int64_t gi, int buf) {
-        const int64_t s0 = group_first(gi);
         const int nb = group_size(gi);
         for (int b = 0; b < nb; ++b) {
-            const float *src = a.in + (s0 + b * s_step) * a.plane;
+            const float *src = a.in + slice_of(gi, b) * a.plane;
             float *db = ds + (int64_t)buf * B * R * ss + (b / W) * W * R * ss + b % W;
             if (a.pt_stride == 1) {
                 for (int r = 0; r < lines_here; ++r) {
@@ -431,7 +436,6 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     if (dbl && g_first < ngroups) issue_loads(g_first, 0);
     int buf = 0;
     for (int64_t gi = g_first; gi < ngroups; gi += g_step, buf ^= (dbl ? 1 : 0)) {
-        const int64_t s0 = group_first(gi);
         const int nb = group_size(gi);
         if (!dbl) issue_loads(gi, 0);
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -500,7 +504,7 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
         __syncthreads();
         // ---- store
         for (int b = 0; b < nb; ++b) {
-            float *dst = a.out + (s0 + b * s_step) * a.plane;
+            float *dst = a.out + slice_of(gi, b) * a.plane;
             const float *db = ds + (int64_t)buf * B * R * ss + (b / W) * W * R * ss + b % W;
             if (a.pt_stride == 1) {
                 for (int r = 0; r < lines_here; ++r) {
