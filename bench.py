@@ -7,10 +7,11 @@ paper, Sec. 4).  One step = one 3rd-RF forward application V_H x and one
 adjoint application V_H^T y over the whole batch (56.6 M grid points each).
 Metric: grid points through one V_H application per second (forward and
 adjoint each count), i.e. 2 * points / step time.  The 1st-RF x5 filter is
-timed the same way for the speed-up.  Each field (226 MB per variable, 453 MB
-per step input) is larger than the 126 MB L2, so no L2 flush is needed.
+timed the same way for the speed-up.  The field (113 MB per variable, 226 MB
+for T and S) is larger than the 126 MB L2, so no L2 flush is needed.
+`--levels N` runs the first N levels only (a smaller case for profiling).
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--levels N]
 Under torchrun each rank runs its own batch (weak scaling, no data-path
 collective); rank 0 prints one JSON line.
 """
@@ -31,7 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gpts/s of V_h 3rd-RF fwd+adjoint vs 1st-RF x5; % of HBM roofline"
-WORKLOAD = "regional basin 1024x384x72, T+S, 30% land, L in [5,40] (fwd+adjoint)"
+def workload_name(nz: int) -> str:
+    return f"regional basin 1024x384x{nz}, T+S, 30% land, L in [5,40] (fwd+adjoint)"
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -44,6 +46,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="bound on the CPU oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--levels", type=int, default=None,
+                   help="use only the first N of the 72 levels (a smaller case for profiling)")
     return p.parse_args()
 
 
@@ -73,14 +77,15 @@ def source_hash() -> str:
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
+    """DRAM bytes of one V_H application (its x and y launches) from the
+    committed ncu summary, if it was taken on the current kernel sources
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         if rec.get("source_hash") == source_hash():
-            return float(rec["dram_bytes_per_launch"])
+            return float(rec["dram_bytes_per_application"])
     except Exception:
         pass
     return None
@@ -142,9 +147,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def make_inputs(nvar_override=None):
+def make_inputs(levels=None):
     from paper_1404_5756_gb300 import synth
-    return synth.workload(2, nvar=nvar_override)
+    return synth.workload(2, nz=levels)
 
 
 def cpu_oracle_sample(w, seconds: float, order=3, iters=1):
@@ -175,7 +180,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = make_inputs()
+    w = make_inputs(args.levels)
     npts = w["nvar"] * w["nz"] * w["nx"] * w["ny"]
     per_step = []
     for _ in range(args.warmup):
@@ -190,7 +195,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 2 * npts / (val * 1e9) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": w["nx"], "ny": w["ny"], "nz": w["nz"],
+        "config": {"workload": workload_name(w["nz"]), "nx": w["nx"], "ny": w["ny"], "nz": w["nz"],
                    "nvar": w["nvar"]},
         "cpu_baseline": {"value": val, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -200,9 +205,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def timed_loop(torch, plan, x, y, z, steps, warmup, stream, events=True):
+def timed_loop(torch, plan, x, y, z, steps, warmup, stream, tag):
     """Warm up, then time `steps` fwd+adjoint steps with CUDA events on the
-    launching stream; also per-application events for the roofline."""
+    launching stream; also per-application events for the roofline.  The
+    timed launches sit in the NVTX range `tag` (for ncu --nvtx-include)."""
     for _ in range(warmup):
         plan.apply(x, out=y)
         plan.apply_adjoint(y, out=z)
@@ -211,6 +217,7 @@ def timed_loop(torch, plan, x, y, z, steps, warmup, stream, events=True):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push(tag)
     start.record(stream)
     for e0, e1, e2 in ev:
         e0.record(stream)
@@ -219,6 +226,7 @@ def timed_loop(torch, plan, x, y, z, steps, warmup, stream, events=True):
         plan.apply_adjoint(y, out=z)
         e2.record(stream)
     stop.record(stream)
+    torch.cuda.nvtx.range_pop()
     stop.synchronize()
     total_ms = start.elapsed_time(stop)
     fwd = [a.elapsed_time(b) for a, b, _ in ev]
@@ -237,7 +245,7 @@ def run_gpu(args):
 
     from paper_1404_5756_gb300 import Options, Plan
 
-    w = make_inputs()
+    w = make_inputs(args.levels)
     nvar, nz, ny, nx = w["x"].shape
     npts = nvar * nz * ny * nx
     plan3 = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=nz), Options(order=3),
@@ -262,7 +270,7 @@ def run_gpu(args):
     barrier()
     with ClockSampler(local) as clk:
         total_ms, fwd_ms, adj_ms, launches = timed_loop(torch, plan3, x, y, z, args.steps,
-                                                        args.warmup, stream)
+                                                        args.warmup, stream, "rf3_timed")
     barrier()
     total_ms = max_over_ranks(torch, world, total_ms)
     ms_step = total_ms / args.steps
@@ -270,7 +278,8 @@ def run_gpu(args):
 
     # ---- 1st-RF x5, same protocol
     barrier()
-    t1_ms, f1, a1, _ = timed_loop(torch, plan1, x, y, z, args.steps, args.warmup, stream)
+    t1_ms, f1, a1, _ = timed_loop(torch, plan1, x, y, z, args.steps, args.warmup, stream,
+                                  "rf1x5_timed")
     t1_ms = max_over_ranks(torch, world, t1_ms)
     value1 = world * 2 * npts / (t1_ms / args.steps * 1e-3) / 1e9
 
@@ -303,7 +312,7 @@ def run_gpu(args):
     achieved = alg_bytes / t_app / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy bandwidth)",
-                "traffic": profiled_traffic(),
+                "traffic": profiled_traffic(), "traffic_unit": "DRAM bytes per application",
                 "unit_of_work": "one V_h application (fwd or adjoint) over the batch",
                 "alg_bytes_per_application": alg_bytes,
                 "launches_per_application": launches / (2 * args.steps)}
@@ -317,8 +326,8 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "nz": nz, "nvar": nvar,
-                   "points_per_step": 2 * npts, "l2": "inputs larger than L2 (453 MB field)",
+        "config": {"workload": workload_name(nz), "nx": nx, "ny": ny, "nz": nz, "nvar": nvar,
+                   "points_per_step": 2 * npts, "l2": f"inputs larger than L2 ({4 * npts / 1e6:.0f} MB field)",
                    "parallelism": f"replicas/level batches x{world}"},
         "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
         "rf1x5": {"value": value1, "unit": "Gpts/s", "ms_per_step": t1_ms / args.steps,
