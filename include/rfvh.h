@@ -60,6 +60,7 @@ enum {
 };
 
 typedef struct rf_plan_ *rf_plan;
+typedef struct rf_graph_ *rf_graph;
 
 /* One domain's grid. */
 typedef struct {
@@ -114,6 +115,10 @@ rf_status rf_coeffs(const rf_grid *grids, int ndomains,
  *                     [nvar][nz][ny][nx]; in[d] == out[d] is allowed;
  *                     distinct domains must not overlap
  *   nvar              variables per domain (e.g. 2 for T and S), >= 1
+ * With several domains the x pass of all domains is one persistent launch
+ * over a work list of (domain, line block, slice group) items, then the y
+ * pass likewise (per 32 domains), unless rf_plan_tune found separate
+ * per-domain launches faster.
  * Asynchronous on `stream`.  Errors: RF_EINVAL (null plan or pointers,
  * nvar < 1), RF_ENOMEM (scratch growth), RF_ECUDA (launch failure). */
 rf_status rf_apply(rf_plan p, const float *const *in, float *const *out,
@@ -166,6 +171,31 @@ rf_status rf_apply_static(rf_plan p, const float *const *in, float *const *out,
  * nvar.  Without tuning a fixed rule picks the shape.  Synchronises `stream`.
  * Errors: RF_EINVAL (null plan, nvar < 1), RF_ENOMEM, RF_ECUDA. */
 rf_status rf_plan_tune(rf_plan p, int nvar, void *stream);
+
+/* CUDA graph of one application: captures rf_apply (adjoint == 0) or
+ * rf_apply_adjoint (adjoint != 0) of the given buffers and nvar into an
+ * executable graph, so a loop that applies the operator many times (a
+ * minimisation) pays one graph launch per application.
+ *   in[d], out[d], nvar   as rf_apply; the graph keeps these pointers, so
+ *                         the buffers must outlive it
+ *   g                     receives the graph; untouched on error
+ * Chooses launch shapes and grows the plan's scratch before capturing, so
+ * the captured call allocates nothing; the capture runs on a private stream
+ * and launches nothing.  Call rf_plan_tune first if tuned shapes are wanted:
+ * later tuning does not change an existing graph.  The graph uses the plan's
+ * buffers: destroy graphs before their plan, and do not replay a graph
+ * concurrently with another use of the same plan.
+ * Errors: RF_EINVAL, RF_ENOMEM, RF_ECUDA. */
+rf_status rf_graph_create(rf_plan p, const float *const *in, float *const *out,
+                          int nvar, int adjoint, rf_graph *g);
+
+/* Replays the graph on `stream` (asynchronous).  Errors: RF_EINVAL (null
+ * graph), RF_ECUDA. */
+rf_status rf_graph_launch(rf_graph g, void *stream);
+
+/* Frees the graph (after the work it launched has finished).  NULL is
+ * accepted. */
+rf_status rf_graph_destroy(rf_graph g);
 
 /* Sticky status of the plan: RF_OK, or the first error a launch or a
  * device-side check recorded since the plan was built. */

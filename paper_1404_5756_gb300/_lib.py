@@ -75,12 +75,15 @@ def load(build_if_missing: bool = False):
     lib.rf_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i),
                                  ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.rf_plan_destroy.argtypes = [vp]
+    lib.rf_graph_create.argtypes = [vp, pp, pp, i, i, ctypes.POINTER(vp)]
+    lib.rf_graph_launch.argtypes = [vp, vp]
+    lib.rf_graph_destroy.argtypes = [vp]
     lib.rf_status_string.argtypes = [i]
     lib.rf_status_string.restype = ctypes.c_char_p
     for name in ("rf_options_default", "rf_coeffs", "rf_apply", "rf_apply_adjoint",
                  "rf_apply_host", "rf_apply_static", "rf_plan_tune", "rf_plan_status",
-                 "rf_plan_info",
-                 "rf_plan_destroy"):
+                 "rf_plan_info", "rf_plan_destroy", "rf_graph_create", "rf_graph_launch",
+                 "rf_graph_destroy"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -158,3 +161,18 @@ def rf_plan_info(plan):
 
 def rf_plan_destroy(plan) -> None:
     check(load().rf_plan_destroy(plan), "rf_plan_destroy")
+
+
+def rf_graph_create(plan, ins, outs, nvar, adjoint) -> ctypes.c_void_p:
+    g = ctypes.c_void_p()
+    check(load().rf_graph_create(plan, ptr_array(ins), ptr_array(outs), int(nvar),
+                                 int(bool(adjoint)), ctypes.byref(g)), "rf_graph_create")
+    return g
+
+
+def rf_graph_launch(graph, stream) -> None:
+    check(load().rf_graph_launch(graph, ctypes.c_void_p(stream)), "rf_graph_launch")
+
+
+def rf_graph_destroy(graph) -> None:
+    check(load().rf_graph_destroy(graph), "rf_graph_destroy")

@@ -79,12 +79,27 @@ struct Domain {
 
 }  // namespace
 
+namespace {
+// Launch shape of one pass of the multi-domain launch for nvar variables.
+struct MultiCfg {
+    int64_t nvar;
+    bool adjoint;
+    int dir;
+    TileShape sh;
+    size_t smem;
+    int occ;
+};
+}  // namespace
+
 struct rf_plan_ {
     rf_options opt{};
     std::vector<Domain> dom;
     int64_t bytes = 0;
     int64_t launches = 0;
     rf_status sticky = RF_OK;
+    unsigned long long *queue = nullptr;   // work-list counter of multi-domain launches
+    std::vector<MultiCfg> mcfg;            // multi-domain launch shapes chosen so far
+    std::vector<std::pair<int64_t, bool>> multi_pref;   // tuned: (nvar, use multi-domain launches)
 };
 
 namespace {
@@ -120,6 +135,13 @@ void free_domain(Domain &d)
     cudaFree(d.tscr);
     cudaFree(d.stage);
     d = Domain{};
+}
+
+void free_plan(rf_plan_ *p)
+{
+    for (auto &d : p->dom) free_domain(d);
+    cudaFree(p->queue);
+    p->queue = nullptr;
 }
 
 rf_status check_options(const rf_options &o)
@@ -482,12 +504,32 @@ rf_status ensure(float **buf, int64_t *have, int64_t need, int64_t *bytes)
 }
 
 // ------------------------------------------------------------------ apply
+// Raise a kernel's dynamic shared-memory limit once per device and size, so
+// a launch inside a stream capture makes no attribute call.
+constexpr int kAttrDevices = 64;
+template <int ORDER, bool ADJ, int R, int B, bool MULTI>
+void smem_attr(size_t smem)
+{
+    static std::mutex mu;
+    static size_t done[kAttrDevices] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < kAttrDevices && smem <= done[dev]) return;
+    if (MULTI)
+        cudaFuncSetAttribute(tile_multi_kernel<ORDER, ADJ, R, B>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
+        cudaFuncSetAttribute(tile_kernel<ORDER, ADJ, R, B>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= 0 && dev < kAttrDevices) done[dev] = smem;
+}
+
 template <int ORDER, bool ADJ, int R, int B>
 void launch_tile(const TileArgs &a, int64_t nlines, int64_t groups, size_t smem,
                  cudaStream_t st)
 {
-    cudaFuncSetAttribute(tile_kernel<ORDER, ADJ, R, B>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_attr<ORDER, ADJ, R, B, false>(smem);
     dim3 grid((unsigned)((nlines + R - 1) / R), (unsigned)groups);
     tile_kernel<ORDER, ADJ, R, B><<<grid, 32 * R, smem, st>>>(a);
 }
@@ -511,25 +553,30 @@ void launch_shape(const TileArgs &a, TileShape sh, int64_t nlines, int64_t group
 // Tile shape: a CTA's slices are the variables of one level when the
 // coefficients differ per level, else the slices are split for about two
 // waves of CTAs.
-template <int ORDER, bool ADJ, int R, int B>
+template <int ORDER, bool ADJ, int R, int B, bool MULTI = false>
 int tile_occupancy(size_t smem)
 {
-    cudaFuncSetAttribute(tile_kernel<ORDER, ADJ, R, B>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_attr<ORDER, ADJ, R, B, MULTI>(smem);
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_kernel<ORDER, ADJ, R, B>,
-                                                      32 * R, smem) != cudaSuccess) {
+    cudaError_t e;
+    if (MULTI)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &blocks, tile_multi_kernel<ORDER, ADJ, R, B>, 32 * R, smem);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_kernel<ORDER, ADJ, R, B>,
+                                                          32 * R, smem);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return blocks;
 }
 
-template <int ORDER, bool ADJ>
+template <int ORDER, bool ADJ, bool MULTI = false>
 int shape_occupancy(TileShape sh, size_t smem)
 {
 #define RF_SHAPE(r, b) \
-    if (sh.R == r && sh.B == b) return tile_occupancy<ORDER, ADJ, r, b>(smem);
+    if (sh.R == r && sh.B == b) return tile_occupancy<ORDER, ADJ, r, b, MULTI>(smem);
     RF_SHAPE(8, 4) RF_SHAPE(8, 2) RF_SHAPE(8, 1) RF_SHAPE(4, 4) RF_SHAPE(4, 2)
     RF_SHAPE(4, 1) RF_SHAPE(2, 4) RF_SHAPE(2, 1) RF_SHAPE(1, 4) RF_SHAPE(1, 1)
 #undef RF_SHAPE
@@ -646,41 +693,46 @@ std::vector<int64_t> batch_candidates(const Domain &D, int64_t nvar)
     return out;
 }
 
+// Arguments of the tile kernel for direction q of domain D.
+TileArgs tile_args(const Domain &D, const Dir &q, const float *in, float *out, int64_t nvar,
+                   int64_t k0, int64_t nk, int iters, int nbuf)
+{
+    TileArgs a{};
+    a.in = in;
+    a.out = out;
+    a.coef = q.coef_il;
+    a.lanes = q.lanes;
+    a.xfer = q.xfer;
+    a.tail_base = q.tail_base;
+    a.tmap = q.tmap;
+    a.n = q.n;
+    a.nlines = q.nlines;
+    a.C = (int)q.C;
+    a.pt_stride = q.pt_stride;
+    a.line_stride = q.line_stride;
+    a.plane = D.g.nx * D.g.ny;
+    a.nz = D.g.nz;
+    a.nvar = nvar;
+    a.k0 = k0;
+    a.nk = nk;
+    a.ncl = D.ncl;
+    a.iters = iters;
+    a.smem_stride = (int)smem_stride(q.n);
+    a.max_re = q.ntail > 0 ? q.max_re : 0;
+    a.vec4 = q.pt_stride == 1 && q.n % 4 == 0 && ((uintptr_t)in % 16) == 0 &&
+             ((uintptr_t)out % 16) == 0;
+    a.nbuf = nbuf;
+    return a;
+}
+
 template <int ORDER, bool ADJ>
 void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *in,
                 float *out, int64_t nvar, int64_t k0, int64_t nk, int iters, cudaStream_t st)
 {
     const int64_t plane = D.g.nx * D.g.ny;
-    const TileShape sh = L.sh;
-    const size_t smem = L.smem;
-    const int64_t groups = L.groups;
     if (L.tile) {
-        TileArgs a{};
-        a.in = in;
-        a.out = out;
-        a.coef = q.coef_il;
-        a.lanes = q.lanes;
-        a.xfer = q.xfer;
-        a.tail_base = q.tail_base;
-        a.tmap = q.tmap;
-        a.n = q.n;
-        a.nlines = q.nlines;
-        a.C = q.C;
-        a.pt_stride = q.pt_stride;
-        a.line_stride = q.line_stride;
-        a.plane = plane;
-        a.nz = D.g.nz;
-        a.nvar = nvar;
-        a.k0 = k0;
-        a.nk = nk;
-        a.ncl = D.ncl;
-        a.iters = iters;
-        a.smem_stride = (int)smem_stride(q.n);
-        a.max_re = q.ntail > 0 ? q.max_re : 0;
-        a.vec4 = q.pt_stride == 1 && q.n % 4 == 0 && ((uintptr_t)in % 16) == 0 &&
-                 ((uintptr_t)out % 16) == 0;
-        a.nbuf = L.nbuf;
-        launch_shape<ORDER, ADJ>(a, sh, q.nlines, groups, smem, st);
+        const TileArgs a = tile_args(D, q, in, out, nvar, k0, nk, iters, L.nbuf);
+        launch_shape<ORDER, ADJ>(a, L.sh, q.nlines, L.groups, L.smem, st);
     } else {
         LineArgs a{};
         a.in = in;
@@ -719,8 +771,10 @@ LaunchCfg cfg_of(const rf_plan_ *p, Domain &D, int dir, int64_t nvar, int64_t nk
 }
 
 // V_H (or its adjoint) on one domain, in batches of nkb levels.
+// dry: choose the configurations and grow the scratch, but launch nothing
+// (run before a stream capture, so the captured call allocates nothing).
 rf_status apply_domain(rf_plan_ *p, Domain &D, const float *in, float *out, int nvar,
-                       bool adjoint, int64_t nkb, cudaStream_t st)
+                       bool adjoint, int64_t nkb, bool dry, cudaStream_t st)
 {
     const int64_t nz = D.g.nz;
     // global scratch for segment-end states, only for the long-line path
@@ -733,6 +787,11 @@ rf_status apply_domain(rf_plan_ *p, Domain &D, const float *in, float *out, int 
     if (s != RF_OK) return s;
     const int K = p->opt.iters;
     for (int64_t k0 = 0; k0 < nz; k0 += nkb) {
+        if (dry) {
+            cfg_of(p, D, 0, nvar, std::min(nkb, nz - k0), adjoint);
+            cfg_of(p, D, 1, nvar, std::min(nkb, nz - k0), adjoint);
+            continue;
+        }
         const int64_t nk = std::min(nkb, nz - k0);
         for (int pass = 0; pass < 2; ++pass) {
             const int dir = adjoint ? 1 - pass : pass;   // forward x then y
@@ -757,15 +816,197 @@ rf_status apply_domain(rf_plan_ *p, Domain &D, const float *in, float *out, int 
     return RF_OK;
 }
 
+// ------------------------------------------------------ multi-domain launches
+// The tile-kernel domains of one pass share a launch shape.  Per domain the
+// slices one CTA filters (the variables of one level when the coefficients
+// differ per level) must number at least B; the shared memory is the
+// largest domain's.
+bool multi_fits(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, size_t *smem)
+{
+    size_t m = 0;
+    bool any = false;
+    for (const Domain &D : p->dom) {
+        const Dir &q = D.d[dir];
+        if (q.R == 0) continue;
+        const int64_t per_cta = D.ncl > 1 ? nvar : nvar * D.g.nz;
+        if (sh.B > 1 && sh.B > per_cta) return false;
+        m = std::max(m, (size_t)tile_smem_bytes(sh.R, sh.B, smem_stride(q.n), q.max_re, 1));
+        any = true;
+    }
+    *smem = m;
+    return any && m + 64 <= kSmemMax;   // the kernel's own static shared memory
+}
+
+template <int ORDER, bool ADJ>
+bool multi_try(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, MultiCfg &c)
+{
+    size_t smem = 0;
+    if (!multi_fits(p, dir, nvar, sh, &smem)) return false;
+    const int occ = shape_occupancy<ORDER, ADJ, true>(sh, smem);
+    if (occ < 1) return false;
+    c = MultiCfg{nvar, ADJ, dir, sh, smem, occ};
+    return true;
+}
+
+bool multi_try_any(const rf_plan_ *p, int dir, int64_t nvar, bool adjoint, TileShape sh,
+                   MultiCfg &c)
+{
+    if (p->opt.order == 3)
+        return adjoint ? multi_try<3, true>(p, dir, nvar, sh, c)
+                       : multi_try<3, false>(p, dir, nvar, sh, c);
+    return adjoint ? multi_try<1, true>(p, dir, nvar, sh, c) : multi_try<1, false>(p, dir, nvar, sh, c);
+}
+
+// Shape of a pass: tuned, cached, or the first of the direction's preference
+// list that allows two CTAs per SM (else the first that fits).  occ = 0: no
+// domain of the pass runs on the tile kernel.
+MultiCfg multi_cfg(rf_plan_ *p, int dir, int64_t nvar, bool adjoint)
+{
+    for (const MultiCfg &c : p->mcfg)
+        if (c.nvar == nvar && c.adjoint == adjoint && c.dir == dir) return c;
+    MultiCfg c{nvar, adjoint, dir, {0, 0}, 0, 0};
+    bool found = false;
+    for (int pass = 0; pass < 2 && !found; ++pass)
+        for (const TileShape &sh : dir == 1 ? kShapesY : kShapesX) {
+            MultiCfg t;
+            if (multi_try_any(p, dir, nvar, adjoint, sh, t) &&
+                (pass == 1 || t.smem <= kSmemTarget)) {
+                c = t;
+                found = true;
+                break;
+            }
+        }
+    p->mcfg.push_back(c);
+    return c;
+}
+
+template <int ORDER, bool ADJ, int R, int B>
+void launch_multi_rb(const MultiArgs &m, unsigned grid, size_t smem, cudaStream_t st)
+{
+    smem_attr<ORDER, ADJ, R, B, true>(smem);
+    tile_multi_kernel<ORDER, ADJ, R, B><<<grid, 32 * R, smem, st>>>(m);
+}
+
+template <int ORDER, bool ADJ>
+void launch_multi(const MultiArgs &m, TileShape sh, unsigned grid, size_t smem, cudaStream_t st)
+{
+#define RF_SHAPE(r, b)                                                   \
+    if (sh.R == r && sh.B == b) {                                        \
+        launch_multi_rb<ORDER, ADJ, r, b>(m, grid, smem, st);            \
+        return;                                                          \
+    }
+    RF_SHAPE(8, 4) RF_SHAPE(8, 2) RF_SHAPE(8, 1) RF_SHAPE(4, 4) RF_SHAPE(4, 2)
+    RF_SHAPE(4, 1) RF_SHAPE(2, 4) RF_SHAPE(2, 1) RF_SHAPE(1, 4) RF_SHAPE(1, 1)
+#undef RF_SHAPE
+}
+
+// One pass (direction c.dir) over every tile-kernel domain: persistent
+// launches over the work list of up to kMaxMulti domains each.
+rf_status multi_pass(rf_plan_ *p, const MultiCfg &c, const float *const *src,
+                     float *const *out, int nvar, bool adjoint, cudaStream_t st)
+{
+    std::vector<int> doms;
+    for (size_t d = 0; d < p->dom.size(); ++d)
+        if (p->dom[d].d[c.dir].R > 0) doms.push_back((int)d);
+    const int iters = p->opt.order == 3 ? 1 : p->opt.iters;
+    for (size_t c0 = 0; c0 < doms.size(); c0 += kMaxMulti) {
+        MultiArgs m{};
+        m.ndom = (int)std::min<size_t>(kMaxMulti, doms.size() - c0);
+        m.queue = p->queue;
+        int64_t total = 0;
+        for (int k = 0; k < m.ndom; ++k) {
+            const Domain &D = p->dom[doms[c0 + k]];
+            const Dir &q = D.d[c.dir];
+            const int d = doms[c0 + k];
+            m.dom[k] = tile_args(D, q, src[d], out[d], nvar, 0, D.g.nz, iters, 1);
+            m.gx[k] = (q.nlines + c.sh.R - 1) / c.sh.R;
+            m.rows[k] = D.ncl > 1 ? D.g.nz : (nvar * D.g.nz + c.sh.B - 1) / c.sh.B;
+            m.first[k] = total;
+            total += m.gx[k] * m.rows[k];
+        }
+        m.first[m.ndom] = total;
+        const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)num_sms() * c.occ);
+        RF_TRY(cuda_status(cudaMemsetAsync(p->queue, 0, sizeof(unsigned long long), st)));
+        if (p->opt.order == 3) {
+            if (adjoint) launch_multi<3, true>(m, c.sh, grid, c.smem, st);
+            else launch_multi<3, false>(m, c.sh, grid, c.smem, st);
+        } else {
+            if (adjoint) launch_multi<1, true>(m, c.sh, grid, c.smem, st);
+            else launch_multi<1, false>(m, c.sh, grid, c.smem, st);
+        }
+        const rf_status s = cuda_status(cudaGetLastError());
+        if (s != RF_OK) {
+            if (p->sticky == RF_OK) p->sticky = s;
+            return s;
+        }
+        ++p->launches;
+    }
+    return RF_OK;
+}
+
+// Multi-domain application: x over all domains, then y over all domains
+// (adjoint: y then x); the domains too long for the tile kernel in a
+// direction run on the long-line kernel in the same pass.
+rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, int nvar,
+                      bool adjoint, bool dry, cudaStream_t st)
+{
+    if (!p->queue) RF_TRY(dev_alloc(&p->queue, 1, &p->bytes));
+    for (Domain &D : p->dom) {
+        int64_t nt = 0;
+        for (int dir = 0; dir < 2; ++dir)
+            if (D.d[dir].R == 0) nt = std::max(nt, D.d[dir].ntail);
+        RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * D.g.nz * nt * 3, &p->bytes));
+    }
+    const int K = p->opt.iters;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int dir = adjoint ? 1 - pass : pass;
+        const MultiCfg c = multi_cfg(p, dir, nvar, adjoint);
+        if (dry) continue;
+        const float *const *src = pass == 0 ? in : (const float *const *)out;
+        if (c.occ > 0) RF_TRY(multi_pass(p, c, src, out, nvar, adjoint, st));
+        for (size_t d = 0; d < p->dom.size(); ++d) {
+            Domain &D = p->dom[d];
+            const Dir &q = D.d[dir];
+            if (q.R > 0) continue;
+            const LaunchCfg L{};   // long-line kernel
+            if (p->opt.order == 3) {
+                if (adjoint) launch_dir<3, true>(D, q, L, src[d], out[d], nvar, 0, D.g.nz, 1, st);
+                else launch_dir<3, false>(D, q, L, src[d], out[d], nvar, 0, D.g.nz, 1, st);
+            } else {
+                if (adjoint) launch_dir<1, true>(D, q, L, src[d], out[d], nvar, 0, D.g.nz, K, st);
+                else launch_dir<1, false>(D, q, L, src[d], out[d], nvar, 0, D.g.nz, K, st);
+            }
+            const rf_status s = cuda_status(cudaGetLastError());
+            if (s != RF_OK) {
+                if (p->sticky == RF_OK) p->sticky = s;
+                return s;
+            }
+            ++p->launches;
+        }
+    }
+    return RF_OK;
+}
+
+// Several domains go through the multi-domain launches unless the
+// autotuner found the per-domain launches faster.
+bool use_multi(const rf_plan_ *p, int64_t nvar)
+{
+    if (p->dom.size() < 2) return false;
+    for (const auto &e : p->multi_pref)
+        if (e.first == nvar) return e.second;
+    return true;
+}
+
 rf_status apply_impl(rf_plan p, const float *const *in, float *const *out, int nvar,
-                     bool adjoint, cudaStream_t st)
+                     bool adjoint, cudaStream_t st, bool dry = false)
 {
     if (!p || !in || !out || nvar < 1) return RF_EINVAL;
     for (size_t d = 0; d < p->dom.size(); ++d)
         if (!in[d] || !out[d]) return RF_EINVAL;
+    if (use_multi(p, nvar)) return apply_multi(p, in, out, nvar, adjoint, dry, st);
     for (size_t d = 0; d < p->dom.size(); ++d) {
         Domain &D = p->dom[d];
-        RF_TRY(apply_domain(p, D, in[d], out[d], nvar, adjoint, batch_levels(D, nvar), st));
+        RF_TRY(apply_domain(p, D, in[d], out[d], nvar, adjoint, batch_levels(D, nvar), dry, st));
     }
     return RF_OK;
 }
@@ -850,8 +1091,8 @@ rf_status tune_domain(rf_plan_ *p, Domain &D, int nvar, float *buf, int64_t nf, 
         if (rest != nkb) RF_TRY(tune_shapes(p, D, nvar, rest, buf, nf, e0, e1, st));
         for (int rep = 0; rep < 3; ++rep) {   // one warm-up, then two timed
             if (rep == 1) cudaEventRecord(e0, st);
-            RF_TRY(apply_domain(p, D, buf, buf + nf, nvar, false, nkb, st));
-            RF_TRY(apply_domain(p, D, buf + nf, buf, nvar, true, nkb, st));
+            RF_TRY(apply_domain(p, D, buf, buf + nf, nvar, false, nkb, false, st));
+            RF_TRY(apply_domain(p, D, buf + nf, buf, nvar, true, nkb, false, st));
         }
         cudaEventRecord(e1, st);
         RF_TRY(cuda_status(cudaEventSynchronize(e1)));
@@ -870,6 +1111,83 @@ rf_status tune_domain(rf_plan_ *p, Domain &D, int nvar, float *buf, int64_t nf, 
         }
     if (!found) D.batch.push_back({nvar, best_nkb});
     return RF_OK;
+}
+
+// Multi-domain tuning: time every shape that fits for each pass, then whole
+// forward + adjoint applications with multi-domain against per-domain
+// launches, and keep the faster.
+rf_status tune_multi(rf_plan_ *p, int nvar, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st)
+{
+    const size_t nd = p->dom.size();
+    std::vector<float *> bufs(nd, nullptr);
+    std::vector<const float *> ins(nd);
+    std::vector<float *> outs(nd);
+    rf_status s = RF_OK;
+    int64_t dummy = 0;
+    for (size_t d = 0; d < nd && s == RF_OK; ++d) {
+        const Domain &D = p->dom[d];
+        const int64_t nf = (int64_t)nvar * D.g.nz * D.g.nx * D.g.ny;
+        s = dev_alloc(&bufs[d], 2 * nf, &dummy);
+        if (s == RF_OK)
+            s = cuda_status(cudaMemsetAsync(bufs[d], 0, sizeof(float) * 2 * (size_t)nf, st));
+        ins[d] = bufs[d];
+        outs[d] = bufs[d] + nf;
+    }
+    if (s == RF_OK && !p->queue) s = dev_alloc(&p->queue, 1, &p->bytes);
+    auto elapsed = [&](float *ms) -> rf_status {
+        cudaEventRecord(e1, st);
+        RF_TRY(cuda_status(cudaEventSynchronize(e1)));
+        cudaEventElapsedTime(ms, e0, e1);
+        return RF_OK;
+    };
+    for (int adj = 0; adj < 2 && s == RF_OK; ++adj)
+        for (int dir = 0; dir < 2 && s == RF_OK; ++dir) {
+            float best_ms = 0.f;
+            MultiCfg best{nvar, adj != 0, dir, {0, 0}, 0, 0};
+            for (const TileShape &sh : kShapesY) {
+                MultiCfg c;
+                if (!multi_try_any(p, dir, nvar, adj != 0, sh, c)) continue;
+                s = multi_pass(p, c, ins.data(), outs.data(), nvar, adj != 0, st);   // warm-up
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3 && s == RF_OK; ++r)
+                    s = multi_pass(p, c, ins.data(), outs.data(), nvar, adj != 0, st);
+                float ms = 0.f;
+                if (s == RF_OK) s = elapsed(&ms);
+                if (s != RF_OK) break;
+                if (best_ms == 0.f || ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+            if (s != RF_OK || best.occ == 0) continue;
+            bool found = false;
+            for (MultiCfg &e : p->mcfg)
+                if (e.nvar == nvar && e.adjoint == (adj != 0) && e.dir == dir) {
+                    e = best;
+                    found = true;
+                }
+            if (!found) p->mcfg.push_back(best);
+        }
+    // multi-domain against per-domain launches
+    float t[2] = {0.f, 0.f};
+    for (int multi = 0; multi < 2 && s == RF_OK; ++multi) {
+        p->multi_pref.erase(std::remove_if(p->multi_pref.begin(), p->multi_pref.end(),
+                                           [&](const std::pair<int64_t, bool> &e) {
+                                               return e.first == nvar;
+                                           }),
+                            p->multi_pref.end());
+        p->multi_pref.push_back({nvar, multi != 0});
+        for (int rep = 0; rep < 3 && s == RF_OK; ++rep) {   // one warm-up, then two timed
+            if (rep == 1) cudaEventRecord(e0, st);
+            s = apply_impl(p, ins.data(), outs.data(), nvar, false, st);
+            if (s == RF_OK) s = apply_impl(p, (const float *const *)outs.data(), (float *const *)ins.data(), nvar, true, st);
+        }
+        if (s == RF_OK) s = elapsed(&t[multi]);
+    }
+    if (s == RF_OK) p->multi_pref.back().second = t[1] <= t[0];
+    cudaStreamSynchronize(st);
+    for (float *b : bufs) cudaFree(b);
+    return s;
 }
 
 rf_status tune_impl(rf_plan_ *p, int nvar, cudaStream_t st)
@@ -893,6 +1211,7 @@ rf_status tune_impl(rf_plan_ *p, int nvar, cudaStream_t st)
         cudaFree(buf);
         if (s != RF_OK) break;
     }
+    if (s == RF_OK && p->dom.size() > 1) s = tune_multi(p, nvar, e0, e1, st);
     p->launches = launches;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1086,6 +1405,72 @@ rf_status rf_apply_static(rf_plan p, const float *const *in, float *const *out, 
     return RF_OK;
 }
 
+struct rf_graph_ {
+    rf_plan plan = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;   // kernels per replay
+};
+
+rf_status rf_graph_create(rf_plan p, const float *const *in, float *const *out, int nvar,
+                          int adjoint, rf_graph *g)
+{
+    if (!p || !in || !out || nvar < 1 || !g) return RF_EINVAL;
+    *g = nullptr;
+    const bool adj = adjoint != 0;
+    // configurations and scratch first: the captured call must not allocate
+    RF_TRY(apply_impl(p, in, out, nvar, adj, nullptr, true));
+    cudaStream_t cs = nullptr;
+    RF_TRY(cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)));
+    const int64_t launches0 = p->launches;
+    rf_status s = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    cudaGraph_t graph = nullptr;
+    if (s == RF_OK) {
+        s = apply_impl(p, in, out, nvar, adj, cs);
+        const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (s == RF_OK) s = cuda_status(e);
+    }
+    cudaStreamDestroy(cs);
+    const int64_t captured = p->launches - launches0;
+    p->launches = launches0;   // counted when the graph runs
+    cudaGraphExec_t exec = nullptr;
+    if (s == RF_OK) s = cuda_status(cudaGraphInstantiate(&exec, graph, 0));
+    rf_graph_ *G = s == RF_OK ? new (std::nothrow) rf_graph_ : nullptr;
+    if (s == RF_OK && !G) s = RF_ENOMEM;
+    if (s != RF_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    G->plan = p;
+    G->graph = graph;
+    G->exec = exec;
+    G->launches = captured;
+    *g = G;
+    return RF_OK;
+}
+
+rf_status rf_graph_launch(rf_graph g, void *stream)
+{
+    if (!g) return RF_EINVAL;
+    const rf_status s = cuda_status(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    if (s != RF_OK) {
+        if (g->plan->sticky == RF_OK) g->plan->sticky = s;
+        return s;
+    }
+    g->plan->launches += g->launches;
+    return RF_OK;
+}
+
+rf_status rf_graph_destroy(rf_graph g)
+{
+    if (!g) return RF_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return RF_OK;
+}
+
 rf_status rf_plan_tune(rf_plan p, int nvar, void *stream)
 {
     if (!p || nvar < 1) return RF_EINVAL;
@@ -1115,7 +1500,7 @@ rf_status rf_plan_destroy(rf_plan p)
 {
     if (!p) return RF_OK;
     cudaDeviceSynchronize();
-    for (auto &d : p->dom) free_domain(d);
+    free_plan(p);
     delete p;
     return RF_OK;
 }

@@ -319,10 +319,12 @@ __device__ __forceinline__ void apply_line_tails(const float2 *ml, float *const 
     __syncwarp();
 }
 
+// The work of one CTA: line block bx (lines bx*R ..) and CTA row by of gy
+// rows along the slices (see the slice mapping below).
 template <int ORDER, bool ADJ, int R, int B>
-__global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
+__device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t by, int64_t gy,
+                                          unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int XS = XF<ORDER>::size, M = XF<ORDER>::mat;
     constexpr int W = Pack<B>::W, U = Pack<B>::U;
     using L = typename LaneT<W>::L;
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     float2 *ms = reinterpret_cast<float2 *>(smem_raw + 16);
     float *ds = reinterpret_cast<float *>(ms + ((R * mre * 9 + 1) & ~1));
     float *ys = ds + a.nbuf * B * R * ss;   // after the data buffers
-    const int64_t line0 = (int64_t)blockIdx.x * R;
+    const int64_t line0 = bx * R;
     const int64_t myline = line0 + warp;
     const bool active = myline < a.nlines;
     const int lines_here = (int)min((int64_t)R, a.nlines - line0);
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
     // Per-level coefficients: CTA row y is level k0 + y and its groups hold
     // the variables g*B + b of that level.
     const bool one_level = a.ncl == 1;
-    const int64_t lev = one_level ? 0 : a.k0 + blockIdx.y;
+    const int64_t lev = one_level ? 0 : a.k0 + by;
     const int64_t nvar = a.nvar, nitems = a.nvar * a.nk;
     const int64_t ngroups = one_level ? (nitems + B - 1) / B : (nvar + B - 1) / B;
     const int64_t lvl_lines = lev * a.nlines;
@@ -397,8 +399,8 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
 
     // Slice groups of this CTA, double buffered: the copies of the next
     // group are in flight while the current one is filtered.
-    const int64_t g_first = one_level ? blockIdx.y : 0;
-    const int64_t g_step = one_level ? gridDim.y : 1;
+    const int64_t g_first = one_level ? by : 0;
+    const int64_t g_step = one_level ? gy : 1;
     auto slice_of = [&](int64_t gi, int b) -> int64_t {
         const int64_t i = gi * B + b;
         return one_level ? (i / a.nk) * a.nz + a.k0 + i % a.nk : i * a.nz + lev;
@@ -526,6 +528,48 @@ __global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
         if (!dbl) __syncthreads();   // stores read the buffer the next copies fill
     }
     cp_async_wait_all();   // a CTA without slices still owns its map copies
+}
+
+template <int ORDER, bool ADJ, int R, int B>
+__global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_body<ORDER, ADJ, R, B>(a, blockIdx.x, blockIdx.y, gridDim.y, smem_raw);
+}
+
+// Several domains in one launch.  The work list holds, domain after domain,
+// one item per (line block, CTA row) of that domain's own grid: item i of
+// domain d is line block i % gx[d] and row i / gx[d] of rows[d].  Persistent
+// CTAs take items from a queue counter (zeroed by the host before the
+// launch) until the list is exhausted, so ragged domains share the GPU
+// without a tail per domain.
+constexpr int kMaxMulti = 32;
+struct MultiArgs {
+    TileArgs dom[kMaxMulti];
+    int64_t first[kMaxMulti + 1];   // first item of each domain; first[ndom] = total
+    int64_t gx[kMaxMulti];          // line blocks per domain
+    int64_t rows[kMaxMulti];        // CTA rows per domain
+    unsigned long long *queue;      // item counter
+    int ndom;
+};
+
+template <int ORDER, bool ADJ, int R, int B>
+__global__ void __launch_bounds__(32 * R) tile_multi_kernel(const __grid_constant__ MultiArgs m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long item_s;
+    const int64_t total = m.first[m.ndom];
+    for (;;) {
+        __syncthreads();   // the previous item is done with shared memory
+        if (threadIdx.x == 0) item_s = (long long)atomicAdd(m.queue, 1ull);
+        __syncthreads();
+        const int64_t item = item_s;
+        if (item >= total) break;
+        int d = 0;
+        while (d + 1 < m.ndom && m.first[d + 1] <= item) ++d;
+        const int64_t i = item - m.first[d];
+        tile_body<ORDER, ADJ, R, B>(m.dom[d], i % m.gx[d], i / m.gx[d], m.rows[d], smem_raw);
+    }
 }
 
 }  // namespace rfvh

@@ -147,6 +147,22 @@ class Plan:
         """V_H^T x."""
         return self._run(x, out, True)
 
+    def graph(self, x, out, adjoint: bool = False) -> "Graph":
+        """CUDA graph of one application on fixed buffers (rf_graph_create):
+        replaying it computes out = V_H x (adjoint: V_H^T x) for the current
+        contents of x."""
+        single = torch.is_tensor(x)
+        xs = [x] if single else list(x)
+        outs = [out] if single else list(out)
+        nz, ny, nx = self.shapes[0]
+        nvar = xs[0].numel() // (nz * ny * nx)
+        self._check(xs, nvar)
+        self._check(outs, nvar)
+        with torch.cuda.device(self.device):
+            g = _lib.rf_graph_create(self._plan, [t.data_ptr() for t in xs],
+                                     [t.data_ptr() for t in outs], nvar, adjoint)
+        return Graph(self, g, xs + outs)
+
     def apply_host(self, xs, outs, nvar: int, adjoint: bool = False):
         """End-to-end call on host (ideally pinned) CPU tensors: the library
         copies in, applies, copies out and synchronises."""
@@ -160,6 +176,31 @@ class Plan:
             _lib.rf_apply_host(self._plan, [t.data_ptr() for t in xs],
                                [t.data_ptr() for t in outs], nvar, adjoint,
                                _stream_handle(self.device))
+
+
+class Graph:
+    """An executable CUDA graph of one V_H (or V_H^T) application.  Holds
+    its plan and buffers so they outlive it."""
+
+    def __init__(self, plan: Plan, handle, tensors):
+        self.plan = plan
+        self._g = handle
+        self._keep = tensors
+
+    def launch(self) -> None:
+        with torch.cuda.device(self.plan.device):
+            _lib.rf_graph_launch(self._g, _stream_handle(self.plan.device))
+
+    def close(self) -> None:
+        if getattr(self, "_g", None):
+            _lib.rf_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class VhFunction(torch.autograd.Function):

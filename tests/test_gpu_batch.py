@@ -1,0 +1,131 @@
+"""Ragged multi-domain batches: one persistent launch per pass over a work
+list of every domain's (line block, slice group) items, and CUDA graphs of a
+whole application.  Parity with the FP64 oracle per domain (bar 1e-5 of the
+domain's max |oracle|); the multi-domain launch, separate per-domain plans,
+tuned shapes and graph replays must agree bit for bit, since none of them
+changes the arithmetic of a slice."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as orc  # noqa: E402
+from paper_1404_5756_gb300 import Options, Plan, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+FILTERS = [(3, 1), (1, 5)]
+NVAR = 2
+
+
+def batch():
+    """Small ragged domains (seeded recipe of the 64-domain batch, shrunk),
+    one domain whose rows are too long for the tile kernel (2100 points) and
+    one with a mask and length scales that differ per level."""
+    doms = synth.ragged_domains(6, scale=0.1, max_levels=20)
+    rng = np.random.default_rng(55)
+    ny, nx = 12, 2100
+    L = (3.0 + 20.0 * rng.random((ny, nx))).astype(np.float32)
+    m = (rng.random((ny, nx)) > 0.1).astype(np.uint8)
+    doms.append(dict(nx=nx, ny=ny, nz=2, mask=m, Lx=L, Ly=L.copy()))
+    ny, nx, nz = 40, 70, 3
+    m3 = np.stack([np.roll(synth.land_mask(rng, ny, nx, 4.0, 0.3), 3 * k, axis=1) for k in range(nz)])
+    L3 = np.stack([synth.length_field(rng, ny, nx, 8.0, 3.0, 12.0) * (1 + 0.2 * k) for k in range(nz)])
+    doms.append(dict(nx=nx, ny=ny, nz=nz, mask=m3, Lx=L3.astype(np.float32),
+                     Ly=(0.8 * L3).astype(np.float32)))
+    xs = [rng.standard_normal((NVAR, d["nz"], d["ny"], d["nx"])).astype(np.float32) for d in doms]
+    return doms, xs
+
+
+def plan_of(doms, order, K):
+    return Plan([dict(mask=d["mask"], Lx=d["Lx"], Ly=d["Ly"], nz=d["nz"]) for d in doms],
+                Options(order=order, iters=K))
+
+
+def oracle_of(d, x, order, K, adjoint):
+    return orc.vh(x.astype(np.float64), d["mask"], np.asarray(d["Lx"], np.float64),
+                  np.asarray(d["Ly"], np.float64), order=order, iters=K, adjoint=adjoint)
+
+
+@pytest.fixture(scope="module")
+def data():
+    return batch()
+
+
+@pytest.mark.parametrize("order,K", FILTERS)
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_ragged_batch_matches_oracle(data, order, K, adjoint):
+    doms, xs = data
+    plan = plan_of(doms, order, K)
+    ts = [torch.from_numpy(x).cuda() for x in xs]
+    ys = plan.apply_adjoint(ts) if adjoint else plan.apply(ts)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    for d, x, y in zip(doms, xs, ys):
+        o = oracle_of(d, x, order, K, adjoint)
+        err = np.abs(y.cpu().numpy() - o).max() / max(np.abs(o).max(), 1e-300)
+        assert err <= TOL, (d["nx"], d["ny"], d["nz"], err)
+
+
+@pytest.mark.parametrize("order,K", FILTERS)
+def test_multi_domain_launch_equals_separate_plans(data, order, K):
+    doms, xs = data
+    plan = plan_of(doms, order, K)
+    ts = [torch.from_numpy(x).cuda() for x in xs]
+    launches0 = plan.info()[3]
+    fwd, adj = plan.apply(ts), plan.apply_adjoint(ts)
+    # two passes, one launch each for the tile domains, plus the long-row
+    # domain's x pass on the line kernel
+    assert plan.info()[3] - launches0 == 2 * 3
+    for d, t, f, a in zip(doms, ts, fwd, adj):
+        single = plan_of([d], order, K)
+        assert torch.equal(single.apply(t), f)
+        assert torch.equal(single.apply_adjoint(t), a)
+
+
+def test_tuned_batch_gives_identical_results(data):
+    doms, xs = data
+    ts = [torch.from_numpy(x).cuda() for x in xs]
+    for order, K in FILTERS:
+        plan = plan_of(doms, order, K)
+        ref_f, ref_a = plan.apply(ts), plan.apply_adjoint(ts)
+        plan.tune(NVAR)
+        for a, b in zip(plan.apply(ts), ref_f):
+            assert torch.equal(a, b)
+        for a, b in zip(plan.apply_adjoint(ts), ref_a):
+            assert torch.equal(a, b)
+        assert plan.status() == 0
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_graph_replays_the_application(data, adjoint):
+    doms, xs = data
+    plan = plan_of(doms, 3, 1)
+    ts = [torch.from_numpy(x).cuda() for x in xs]
+    outs = [torch.empty_like(t) for t in ts]
+    g = plan.graph(ts, outs, adjoint=adjoint)
+    rng = np.random.default_rng(9)
+    for _ in range(2):   # new input contents each replay
+        for t in ts:
+            t.copy_(torch.from_numpy(rng.standard_normal(tuple(t.shape)).astype(np.float32)))
+        launches0 = plan.info()[3]
+        g.launch()
+        torch.cuda.synchronize()
+        assert plan.info()[3] > launches0
+        ref = plan.apply_adjoint(ts) if adjoint else plan.apply(ts)
+        for a, b in zip(outs, ref):
+            assert torch.equal(a, b)
+    g.close()
+    assert plan.status() == 0
+
+
+def test_graph_of_a_single_domain_plan():
+    w = synth.workload(2, nz=3, nvar=NVAR)
+    plan = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=3))
+    x = torch.from_numpy(w["x"]).cuda()
+    y = torch.empty_like(x)
+    g = plan.graph(x, y)
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(y, plan.apply(x))
+    g.close()
