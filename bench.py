@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="bound on the CPU oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-ragged", action="store_true",
+                   help="skip the 64-domain ragged batch measurement")
     p.add_argument("--levels", type=int, default=None,
                    help="use only the first N of the 72 levels (a smaller case for profiling)")
     return p.parse_args()
@@ -234,6 +236,65 @@ def timed_loop(torch, plan, x, y, z, steps, warmup, stream, tag):
     return total_ms, fwd, adj, plan.info()[3] - launches0
 
 
+def run_ragged(torch, dev, steps, warmup):
+    """The ragged batch: 64 seeded domains (nx in 128..2048, ny in 64..1024,
+    nz in 1..75, 0-40 % land, L in [3, 40]), one variable, N(0,1) fields drawn
+    on the device from a seeded generator.  V_H forward + adjoint per step,
+    (a) as CUDA graphs of the multi-domain persistent launches, (b) through 64
+    separate single-domain plans (two launches per domain per application).
+    The multi-domain shapes come from rf_plan_tune_batch (which also chooses
+    between multi-domain and per-domain launches); the separate plans use
+    their default shapes."""
+    from paper_1404_5756_gb300 import Options, Plan, synth
+    doms = synth.ragged_domains(64)
+    specs = [dict(mask=d["mask"], Lx=d["Lx"], Ly=d["Ly"], nz=d["nz"]) for d in doms]
+    plan = Plan(specs, Options(order=3), device=dev)
+    plan.tune_batch(1)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1405)
+    xs = [torch.randn((1, d["nz"], d["ny"], d["nx"]), generator=gen, device=dev) for d in doms]
+    ys = [torch.empty_like(x) for x in xs]
+    zs = [torch.empty_like(x) for x in xs]
+    npts = sum(x.numel() for x in xs)
+    g_f = plan.graph(xs, ys)
+    g_a = plan.graph(ys, zs, adjoint=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(step):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    l0 = plan.info()[3]
+    ms_graph = timed(lambda: (g_f.launch(), g_a.launch()))
+    launches = (plan.info()[3] - l0) / (2 * (steps + warmup))
+    singles = [Plan(sp, Options(order=3), device=dev) for sp in specs]
+
+    def separate():
+        for pl, x, y in zip(singles, xs, ys):
+            pl.apply(x, out=y)
+        for pl, y, z in zip(singles, ys, zs):
+            pl.apply_adjoint(y, out=z)
+
+    ms_sep = timed(separate)
+    g_f.close()
+    g_a.close()
+    return {"value": 2 * npts / (ms_graph * 1e-3) / 1e9, "unit": "Gpts/s",
+            "ms_per_step": ms_graph, "domains": len(doms), "points": npts,
+            "launches_per_application": launches, "graph": True,
+            "separate_plans": {"value": 2 * npts / (ms_sep * 1e-3) / 1e9, "unit": "Gpts/s",
+                               "ms_per_step": ms_sep, "launches_per_application": 2 * len(doms)},
+            "data": "synthetic: 64 seeded domains, 1 variable, fields from a seeded device "
+                    "generator"}
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -317,6 +378,10 @@ def run_gpu(args):
                 "alg_bytes_per_application": alg_bytes,
                 "launches_per_application": launches / (2 * args.steps)}
 
+    ragged = None
+    if not args.no_ragged and world == 1:
+        ragged = run_ragged(torch, dev, max(3, min(args.steps, 10)), max(args.warmup, 3))
+
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(w, args.cpu_seconds)
@@ -333,6 +398,7 @@ def run_gpu(args):
         "rf1x5": {"value": value1, "unit": "Gpts/s", "ms_per_step": t1_ms / args.steps,
                   "ms_fwd": float(np.mean(f1)), "ms_adj": float(np.mean(a1))},
         "speedup_rf3_over_rf1x5": value / value1,
+        "ragged64": ragged,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": "Gpts/s",
                 "h2d_bytes_per_step": 2 * 4 * npts, "d2h_bytes_per_step": 2 * 4 * npts},

@@ -172,6 +172,15 @@ rf_status rf_apply_static(rf_plan p, const float *const *in, float *const *out,
  * Errors: RF_EINVAL (null plan, nvar < 1), RF_ENOMEM, RF_ECUDA. */
 rf_status rf_plan_tune(rf_plan p, int nvar, void *stream);
 
+/* The multi-domain part of rf_plan_tune alone, for plans of many domains
+ * where tuning every domain separately would take long: times every shape
+ * of the multi-domain launch of each pass (forward and adjoint) and then
+ * whole applications with multi-domain against per-domain launches, keeping
+ * the faster for later calls with the same nvar.  Allocates scratch fields
+ * for all domains at once for the call.  A plan of one domain: no-op.
+ * Synchronises `stream`.  Errors: as rf_plan_tune. */
+rf_status rf_plan_tune_batch(rf_plan p, int nvar, void *stream);
+
 /* CUDA graph of one application: captures rf_apply (adjoint == 0) or
  * rf_apply_adjoint (adjoint != 0) of the given buffers and nvar into an
  * executable graph, so a loop that applies the operator many times (a

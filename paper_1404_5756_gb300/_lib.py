@@ -71,6 +71,7 @@ def load(build_if_missing: bool = False):
     lib.rf_apply_host.argtypes = [vp, pp, pp, i, i, vp]
     lib.rf_apply_static.argtypes = [vp, pp, pp, i, i, vp]
     lib.rf_plan_tune.argtypes = [vp, i, vp]
+    lib.rf_plan_tune_batch.argtypes = [vp, i, vp]
     lib.rf_plan_status.argtypes = [vp]
     lib.rf_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i),
                                  ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -81,7 +82,8 @@ def load(build_if_missing: bool = False):
     lib.rf_status_string.argtypes = [i]
     lib.rf_status_string.restype = ctypes.c_char_p
     for name in ("rf_options_default", "rf_coeffs", "rf_apply", "rf_apply_adjoint",
-                 "rf_apply_host", "rf_apply_static", "rf_plan_tune", "rf_plan_status",
+                 "rf_apply_host", "rf_apply_static", "rf_plan_tune", "rf_plan_tune_batch",
+                 "rf_plan_status",
                  "rf_plan_info", "rf_plan_destroy", "rf_graph_create", "rf_graph_launch",
                  "rf_graph_destroy"):
         getattr(lib, name).restype = i
@@ -145,6 +147,11 @@ def rf_apply_host(plan, ins, outs, nvar, adjoint, stream) -> None:
 
 def rf_plan_tune(plan, nvar, stream) -> None:
     check(load().rf_plan_tune(plan, int(nvar), ctypes.c_void_p(stream)), "rf_plan_tune")
+
+
+def rf_plan_tune_batch(plan, nvar, stream) -> None:
+    check(load().rf_plan_tune_batch(plan, int(nvar), ctypes.c_void_p(stream)),
+          "rf_plan_tune_batch")
 
 
 def rf_plan_status(plan) -> int:

@@ -257,24 +257,25 @@ __global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C,
     if (line >= nlines_total) return;   // whole warps exit together
     const float4 *src = coef + line * n;
     float4 *dst = il + line * C * 32 + lane;
-    unsigned long long bits = 0;
+    unsigned long long bits[2] = {0ull, 0ull};
     for (int j = 0; j < C; ++j) {
         const int64_t k = (int64_t)lane * C + j;
         float4 c = k < n ? src[k] : make_float4(0.f, 0.f, 0.f, -1.f);
         if (__float_as_uint(c.x) >> 31) {
-            bits |= 1ull << j;
+            bits[j >> 6] |= 1ull << (j & 63);
             c.x = fabsf(c.x);
         }
         dst[(int64_t)j * 32] = c;
     }
-    const int nre = __popcll(bits);
+    const int nre = __popcll(bits[0]) + __popcll(bits[1]);
     int incl = nre;
     for (int d = 1; d < 32; d <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= d) incl += t;
     }
     LaneInfo li;
-    li.rebits = bits;
+    li.re.lo = bits[0];
+    li.re.hi = bits[1];
     li.rank0 = incl - nre;
     li.nre = nre;
     lanes[line * 32 + lane] = li;
@@ -817,19 +818,18 @@ rf_status apply_domain(rf_plan_ *p, Domain &D, const float *in, float *out, int 
 }
 
 // ------------------------------------------------------ multi-domain launches
-// The tile-kernel domains of one pass share a launch shape.  Per domain the
-// slices one CTA filters (the variables of one level when the coefficients
-// differ per level) must number at least B; the shared memory is the
-// largest domain's.
+// The tile-kernel domains of one pass share a launch shape and the largest
+// domain's shared memory.  A domain with fewer slices per CTA than B (the
+// variables of one level when its coefficients differ per level) fills its
+// groups partly, which costs idle slots but no correctness.
 bool multi_fits(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, size_t *smem)
 {
+    (void)nvar;
     size_t m = 0;
     bool any = false;
     for (const Domain &D : p->dom) {
         const Dir &q = D.d[dir];
         if (q.R == 0) continue;
-        const int64_t per_cta = D.ncl > 1 ? nvar : nvar * D.g.nz;
-        if (sh.B > 1 && sh.B > per_cta) return false;
         m = std::max(m, (size_t)tile_smem_bytes(sh.R, sh.B, smem_stride(q.n), q.max_re, 1));
         any = true;
     }
@@ -858,8 +858,9 @@ bool multi_try_any(const rf_plan_ *p, int dir, int64_t nvar, bool adjoint, TileS
 }
 
 // Shape of a pass: tuned, cached, or the first of the direction's preference
-// list that allows two CTAs per SM (else the first that fits).  occ = 0: no
-// domain of the pass runs on the tile kernel.
+// list that allows two CTAs and eight warps per SM with the largest domain's
+// shared memory (else the first that fits).  occ = 0: no domain of the pass
+// runs on the tile kernel.
 MultiCfg multi_cfg(rf_plan_ *p, int dir, int64_t nvar, bool adjoint)
 {
     for (const MultiCfg &c : p->mcfg)
@@ -870,7 +871,7 @@ MultiCfg multi_cfg(rf_plan_ *p, int dir, int64_t nvar, bool adjoint)
         for (const TileShape &sh : dir == 1 ? kShapesY : kShapesX) {
             MultiCfg t;
             if (multi_try_any(p, dir, nvar, adjoint, sh, t) &&
-                (pass == 1 || t.smem <= kSmemTarget)) {
+                (pass == 1 || (t.smem <= kSmemTarget && t.occ * sh.R >= 8))) {
                 c = t;
                 found = true;
                 break;
@@ -1469,6 +1470,25 @@ rf_status rf_graph_destroy(rf_graph g)
     if (g->graph) cudaGraphDestroy(g->graph);
     delete g;
     return RF_OK;
+}
+
+rf_status rf_plan_tune_batch(rf_plan p, int nvar, void *stream)
+{
+    if (!p || nvar < 1) return RF_EINVAL;
+    if (p->dom.size() < 2) return RF_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return RF_ECUDA;
+    }
+    const int64_t launches = p->launches;
+    rf_status s = tune_multi(p, nvar, e0, e1, (cudaStream_t)stream);
+    p->launches = launches;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == RF_OK) s = cuda_status(cudaGetLastError());
+    return s;
 }
 
 rf_status rf_plan_tune(rf_plan p, int nvar, void *stream)

@@ -1,6 +1,6 @@
 // rf_tile.cuh -- the main filter kernel: R whole lines per CTA, one warp per
 // line, the 32 lanes of a warp owning consecutive chunks of C points (C odd,
-// 32*C >= n, C <= 64).  Each thread filters B slices of its chunk at once (B
+// 32*C >= n, C <= 128).  Each thread filters B slices of its chunk at once (B
 // independent recursions: instruction-level parallelism, and one coefficient
 // read serves B slices).  The line data of the B slices and the coastal
 // boundary maps of the CTA's lines sit in shared memory; the per-point
@@ -32,11 +32,45 @@
 
 namespace rfvh {
 
+// Segment ends of one chunk: bit j marks point j.  Bits64 serves chunks of
+// up to 64 points (the common case, one 64-bit word), SegBits chunks of up
+// to 128 (lo: points 0..63, hi: 64..127); both give the sweeps the same
+// interface.
+struct Bits64 {
+    unsigned long long v;
+    __device__ __forceinline__ int first() const { return v ? __ffsll((long long)v) - 1 : 64; }
+    __device__ __forceinline__ int last() const { return v ? 63 - __clzll((long long)v) : -1; }
+    __device__ __forceinline__ void drop_first() { v &= v - 1; }
+    __device__ __forceinline__ void drop(int j) { v &= ~(1ull << j); }
+};
+
+struct SegBits {
+    unsigned long long lo, hi;
+    __device__ __forceinline__ int first() const   // lowest marked point, 128 if none
+    {
+        return lo ? __ffsll((long long)lo) - 1 : hi ? 63 + __ffsll((long long)hi) : 128;
+    }
+    __device__ __forceinline__ int last() const    // highest marked point, -1 if none
+    {
+        return hi ? 127 - __clzll((long long)hi) : lo ? 63 - __clzll((long long)lo) : -1;
+    }
+    __device__ __forceinline__ void drop_first()
+    {
+        if (lo) lo &= lo - 1;
+        else hi &= hi - 1;
+    }
+    __device__ __forceinline__ void drop(int j)
+    {
+        if (j < 64) lo &= ~(1ull << j);
+        else hi &= ~(1ull << (j - 64));
+    }
+};
+
 // Per (line, lane) record of the segment ends in the lane's chunk.
 struct LaneInfo {
-    unsigned long long rebits;   // bit j: point lane*C + j ends a segment
-    int rank0;                   // segment ends on the line before this chunk
-    int nre;                     // segment ends in this chunk
+    SegBits re;    // segment ends in the chunk
+    int rank0;     // segment ends on the line before this chunk
+    int nre;       // segment ends in this chunk
 };
 
 struct TileArgs {
@@ -55,7 +89,7 @@ struct TileArgs {
     int64_t nvar;             // variables of the field
     int64_t k0, nk;           // this launch filters levels k0 .. k0+nk-1
     int64_t ncl;              // coefficient levels (1 or nz)
-    int C;                    // chunk length (odd, <= 64)
+    int C;                    // chunk length (odd, <= 128)
     int iters;
     int smem_stride;          // floats per line row in shared memory
     int max_re;               // boundary-map slots per line (0: no maps)
@@ -63,7 +97,7 @@ struct TileArgs {
     int nbuf;                 // data buffers: 1 or 2 (copies overlap filtering)
 };
 
-constexpr int kMaxChunk = 64;
+constexpr int kMaxChunk = 128;
 // float4 guard entries before and after the interleaved coefficient array,
 // so the sweeps may prefetch up to two steps past either end of a chunk
 constexpr int kCoefGuard = 64;
@@ -217,10 +251,11 @@ struct LaneT<2> {
 // (rank counting down from rk), or to zero without maps.  Coefficients are
 // fetched two steps ahead and data one step ahead, so memory latency
 // overlaps the arithmetic.
-template <int ORDER, bool ADJ, int B, bool CAUSAL, bool IN_SEA, bool WRITE, bool TAILS>
+template <int ORDER, bool ADJ, int B, bool CAUSAL, bool IN_SEA, bool WRITE, bool TAILS,
+          class MASK>
 __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
                                       typename LaneT<Pack<B>::W>::L::T *const *dp, int len,
-                                      uint64_t rebits, const float2 *ml, float *const *ys, int rk,
+                                      MASK rebits, const float2 *ml, float *const *ys, int rk,
                                       typename LaneT<Pack<B>::W>::L::T (*st)[3])
 {
     constexpr int W = Pack<B>::W, U = Pack<B>::U, NS = ORDER == 3 ? 3 : 1;
@@ -230,8 +265,8 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
     const int dir = CAUSAL ? 1 : -1;
     int j = CAUSAL ? 0 : len - 1;
     int re_next;
-    if (CAUSAL) re_next = rebits ? __ffsll((long long)rebits) - 1 : 64;
-    else re_next = rebits ? 63 - __clzll((long long)rebits) : -1;
+    if (CAUSAL) re_next = rebits.first();
+    else re_next = rebits.last();
     float4 c = __ldg(cp + 32 * j);
     float4 c1 = __ldg(cp + 32 * (j + dir));
     T x[U];
@@ -281,11 +316,11 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
         }
         if (at_end) {
             if (CAUSAL) {
-                rebits &= rebits - 1;
-                re_next = rebits ? __ffsll((long long)rebits) - 1 : 64;
+                rebits.drop_first();
+                re_next = rebits.first();
             } else {
-                rebits &= ~((uint64_t)1 << j);
-                re_next = rebits ? 63 - __clzll((long long)rebits) : -1;
+                rebits.drop(j);
+                re_next = rebits.last();
             }
         }
         c = c1;
@@ -365,12 +400,12 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     const int ka = min(lane * C, n), kb = min(ka + C, n), len = kb - ka;
     const float4 *cg = a.coef + ((lvl_lines + min(myline, a.nlines - 1)) * C) * 32 + lane;
     const float2 *ml = ms + warp * mre * 9;
-    uint64_t rebits = 0;
+    SegBits rebits{0ull, 0ull};
     int rank0 = 0, nre = 0, line_re = 0;
     float Pc[M], Pa[M];
     if (active) {
         const LaneInfo li = a.lanes[(lvl_lines + myline) * 32 + lane];
-        rebits = li.rebits;
+        rebits = li.re;
         rank0 = li.rank0;
         nre = li.nre;
         if (mre > 0)
@@ -445,14 +480,16 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
         if (dbl && gi + g_step < ngroups) issue_loads(gi + g_step, buf ^ 1);
 #pragma unroll
         for (int u = 0; u < U; ++u) dl[u] = dt + ((int64_t)buf * U * R + u * R + warp) * ss + ka;
-        if (active) {
+        // the filter work of the group, for the chunk's segment-end mask type
+        auto filter = [&](auto rebits) {
+            using MASK = decltype(rebits);
             for (int it = 0; it < a.iters; ++it) {
                 T st[U][3];
                 float v[B][3], P[M];
                 // ---- A: causal, zero start -> chunk end state (land input zeroed)
 #pragma unroll
                 for (int u = 0; u < U; ++u) st[u][0] = st[u][1] = st[u][2] = L::zero();
-                sweep<ORDER, ADJ, B, true, true, false, false>(cg, dl, len, 0, ml, yl, 0, st);
+                sweep<ORDER, ADJ, B, true, true, false, false>(cg, dl, len, MASK{}, ml, yl, 0, st);
 #pragma unroll
                 for (int b = 0; b < B; ++b)
 #pragma unroll
@@ -502,6 +539,10 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
                 else sweep<ORDER, ADJ, B, false, false, true, false>(cg, dl, len, rebits, ml, yl, 0, st);
                 __syncwarp();
             }
+        };
+        if (active) {
+            if (C <= 64) filter(Bits64{rebits.lo});
+            else filter(rebits);
         }
         __syncthreads();
         // ---- store

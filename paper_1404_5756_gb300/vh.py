@@ -98,6 +98,11 @@ class Plan:
         with torch.cuda.device(self.device):
             _lib.rf_plan_tune(self._plan, nvar, _stream_handle(self.device))
 
+    def tune_batch(self, nvar: int) -> None:
+        """Tune only the multi-domain launches (rf_plan_tune_batch)."""
+        with torch.cuda.device(self.device):
+            _lib.rf_plan_tune_batch(self._plan, nvar, _stream_handle(self.device))
+
     def status(self) -> int:
         return _lib.rf_plan_status(self._plan)
 

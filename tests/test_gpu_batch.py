@@ -20,11 +20,11 @@ NVAR = 2
 
 def batch():
     """Small ragged domains (seeded recipe of the 64-domain batch, shrunk),
-    one domain whose rows are too long for the tile kernel (2100 points) and
+    one domain whose rows are too long for the tile kernel (4200 points) and
     one with a mask and length scales that differ per level."""
     doms = synth.ragged_domains(6, scale=0.1, max_levels=20)
     rng = np.random.default_rng(55)
-    ny, nx = 12, 2100
+    ny, nx = 12, 4200
     L = (3.0 + 20.0 * rng.random((ny, nx))).astype(np.float32)
     m = (rng.random((ny, nx)) > 0.1).astype(np.uint8)
     doms.append(dict(nx=nx, ny=ny, nz=2, mask=m, Lx=L, Ly=L.copy()))

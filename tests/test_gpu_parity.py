@@ -240,12 +240,15 @@ def test_tuned_shapes_give_identical_results():
 
 
 @pytest.mark.parametrize("order,K", FILTERS)
-def test_long_lines_use_the_line_kernel(order, K):
-    """Rows of 3000 points are longer than the tile kernel takes (32 chunks
-    of at most 64 points): the one-thread-per-line kernel with its global
-    scratch for the coastal start states filters them."""
+@pytest.mark.parametrize("nx", [3000, 4200])
+def test_long_lines(order, K, nx):
+    """Rows of 3000 points fill chunks of 95 points, so segment ends fall in
+    both halves of the tile kernel's 128-bit per-chunk masks.  Rows of 4200
+    points are longer than the tile kernel takes (32 chunks of at most 127
+    points): the one-thread-per-line kernel with its global scratch for the
+    coastal start states filters them."""
     rng = np.random.default_rng(30)
-    ny, nx = 6, 3000
+    ny = 6
     mask = (rng.uniform(size=(ny, nx)) > 0.15).astype(np.uint8)
     L = rng.uniform(2.0, 30.0, (ny, nx)).astype(np.float32)
     w = dict(mask=mask, Lx=L, Ly=L)
