@@ -98,6 +98,8 @@ struct rf_plan_ {
     int64_t launches = 0;
     rf_status sticky = RF_OK;
     unsigned long long *queue = nullptr;   // work-list counter of multi-domain launches
+    cudaStream_t s_in = nullptr, s_out = nullptr;   // copy streams of the host-buffer apply
+    cudaEvent_t ev_in = nullptr, ev_done = nullptr, ev_out = nullptr;
     std::vector<MultiCfg> mcfg;            // multi-domain launch shapes chosen so far
     std::vector<std::pair<int64_t, bool>> multi_pref;   // tuned: (nvar, use multi-domain launches)
 };
@@ -142,6 +144,11 @@ void free_plan(rf_plan_ *p)
     for (auto &d : p->dom) free_domain(d);
     cudaFree(p->queue);
     p->queue = nullptr;
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_done) cudaEventDestroy(p->ev_done);
+    if (p->ev_out) cudaEventDestroy(p->ev_out);
 }
 
 rf_status check_options(const rf_options &o)
@@ -1191,6 +1198,91 @@ rf_status tune_multi(rf_plan_ *p, int nvar, cudaEvent_t e0, cudaEvent_t e1, cuda
     return s;
 }
 
+// ------------------------------------------------------ host-buffer apply
+// Copy streams and events of the host-buffer apply, created on first use.
+rf_status host_streams(rf_plan_ *p)
+{
+    if (p->s_in) return RF_OK;
+    cudaStream_t a = nullptr, b = nullptr;
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    rf_status s = cuda_status(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    if (s == RF_OK) s = cuda_status(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+    for (int k = 0; k < 3 && s == RF_OK; ++k)
+        s = cuda_status(cudaEventCreateWithFlags(&e[k], cudaEventDisableTiming));
+    if (s != RF_OK) {
+        if (a) cudaStreamDestroy(a);
+        if (b) cudaStreamDestroy(b);
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+        return s;
+    }
+    p->s_in = a;
+    p->s_out = b;
+    p->ev_in = e[0];
+    p->ev_done = e[1];
+    p->ev_out = e[2];
+    return RF_OK;
+}
+
+constexpr int64_t kHostBatches = 8;
+
+// One domain through host buffers, pipelined over batches of levels: the
+// copy in of a batch (stream s_in), its x and y launches (the caller's
+// stream) and its copy out (stream s_out) overlap with the neighbouring
+// batches'.  Each copy moves the batch's levels of all variables as one
+// pitched 2-D copy (one row of nk levels per variable).
+rf_status host_pipeline(rf_plan_ *p, Domain &D, const float *in, float *out, int nvar,
+                        bool adjoint, cudaStream_t st)
+{
+    const int64_t nz = D.g.nz, plane = D.g.nx * D.g.ny;
+    const int64_t n = (int64_t)nvar * nz * plane;
+    RF_TRY(ensure(&D.stage, &D.stage_floats, n, &p->bytes));
+    const int64_t nkb = (nz + kHostBatches - 1) / kHostBatches;
+    int64_t nt = 0;   // scratch of the long-line kernel
+    for (int dir = 0; dir < 2; ++dir)
+        if (!cfg_of(p, D, dir, nvar, nkb, adjoint).tile ||
+            !cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint).tile)
+            nt = std::max(nt, D.d[dir].ntail);
+    RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 3, &p->bytes));
+    const size_t pitch = (size_t)(nz * plane) * sizeof(float);
+    const int K = p->opt.iters;
+    // (a domain's stage is free here: every earlier host-buffer call ended
+    // with its copies out complete, and nothing else uses the stage)
+    for (int64_t k0 = 0; k0 < nz; k0 += nkb) {
+        const int64_t nk = std::min(nkb, nz - k0);
+        const size_t width = (size_t)(nk * plane) * sizeof(float);
+        float *dev = D.stage + k0 * plane;
+        RF_TRY(cuda_status(cudaMemcpy2DAsync(dev, pitch, in + k0 * plane, pitch, width,
+                                             (size_t)nvar, cudaMemcpyHostToDevice, p->s_in)));
+        RF_TRY(cuda_status(cudaEventRecord(p->ev_in, p->s_in)));
+        RF_TRY(cuda_status(cudaStreamWaitEvent(st, p->ev_in, 0)));
+        for (int pass = 0; pass < 2; ++pass) {
+            const int dir = adjoint ? 1 - pass : pass;
+            const Dir &q = D.d[dir];
+            const LaunchCfg L = cfg_of(p, D, dir, nvar, nk, adjoint);
+            if (p->opt.order == 3) {
+                if (adjoint) launch_dir<3, true>(D, q, L, D.stage, D.stage, nvar, k0, nk, 1, st);
+                else launch_dir<3, false>(D, q, L, D.stage, D.stage, nvar, k0, nk, 1, st);
+            } else {
+                if (adjoint) launch_dir<1, true>(D, q, L, D.stage, D.stage, nvar, k0, nk, K, st);
+                else launch_dir<1, false>(D, q, L, D.stage, D.stage, nvar, k0, nk, K, st);
+            }
+            const rf_status s = cuda_status(cudaGetLastError());
+            if (s != RF_OK) {
+                if (p->sticky == RF_OK) p->sticky = s;
+                return s;
+            }
+            ++p->launches;
+        }
+        RF_TRY(cuda_status(cudaEventRecord(p->ev_done, st)));
+        RF_TRY(cuda_status(cudaStreamWaitEvent(p->s_out, p->ev_done, 0)));
+        RF_TRY(cuda_status(cudaMemcpy2DAsync(out + k0 * plane, pitch, dev, pitch, width,
+                                             (size_t)nvar, cudaMemcpyDeviceToHost, p->s_out)));
+    }
+    RF_TRY(cuda_status(cudaEventRecord(p->ev_out, p->s_out)));
+    return cuda_status(cudaStreamWaitEvent(st, p->ev_out, 0));
+}
+
 rf_status tune_impl(rf_plan_ *p, int nvar, cudaStream_t st)
 {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1281,26 +1373,13 @@ rf_status rf_apply_host(rf_plan p, const float *const *in, float *const *out,
                         int nvar, int adjoint, void *stream)
 {
     if (!p || !in || !out || nvar < 1) return RF_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t nd = p->dom.size();
-    std::vector<const float *> din(nd);
-    std::vector<float *> dout(nd);
-    for (size_t d = 0; d < nd; ++d) {
-        Domain &D = p->dom[d];
+    for (size_t d = 0; d < p->dom.size(); ++d)
         if (!in[d] || !out[d]) return RF_EINVAL;
-        const int64_t n = (int64_t)nvar * D.g.nz * D.g.ny * D.g.nx;
-        RF_TRY(ensure(&D.stage, &D.stage_floats, n, &p->bytes));
-        RF_TRY(cuda_status(cudaMemcpyAsync(D.stage, in[d], (size_t)n * 4,
-                                           cudaMemcpyHostToDevice, st)));
-        din[d] = D.stage;
-        dout[d] = D.stage;
-    }
-    RF_TRY(apply_impl(p, din.data(), dout.data(), nvar, adjoint != 0, st));
-    for (size_t d = 0; d < nd; ++d) {
-        Domain &D = p->dom[d];
-        const int64_t n = (int64_t)nvar * D.g.nz * D.g.ny * D.g.nx;
-        RF_TRY(cuda_status(cudaMemcpyAsync(out[d], D.stage, (size_t)n * 4,
-                                           cudaMemcpyDeviceToHost, st)));
+    cudaStream_t st = (cudaStream_t)stream;
+    RF_TRY(host_streams(p));
+    for (Domain &D : p->dom) {
+        const size_t d = (size_t)(&D - p->dom.data());
+        RF_TRY(host_pipeline(p, D, in[d], out[d], nvar, adjoint != 0, st));
     }
     return cuda_status(cudaStreamSynchronize(st));
 }
