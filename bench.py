@@ -47,7 +47,7 @@ def parse():
                    help="bound on the CPU oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-ragged", action="store_true",
-                   help="skip the 64-domain ragged batch measurement")
+                   help="skip the 64-domain ragged batch and the other configurations")
     p.add_argument("--levels", type=int, default=None,
                    help="use only the first N of the 72 levels (a smaller case for profiling)")
     return p.parse_args()
@@ -295,6 +295,65 @@ def run_ragged(torch, dev, steps, warmup):
                     "generator"}
 
 
+def run_configs(torch, dev, steps, warmup, peak):
+    """The other measured configurations.  impulse_256x128: the 256 x 128
+    all-sea grid with L = 10 and a unit impulse, one application per CUDA-graph
+    replay, median of 20 replays timed one by one (launch-latency bound; no
+    roofline).  global_1440x1080x75: one variable on the global grid (30 %
+    land, L from 30 at the equator to 4 at the poles), forward + adjoint per
+    step after tuning, with its own roofline fraction."""
+    from paper_1404_5756_gb300 import Plan, synth
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    w = synth.workload(1, fields=False)
+    plan = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=1), device=dev)
+    x = torch.from_numpy(synth.impulse(w["ny"], w["nx"], 64, 128)).to(dev)
+    y = torch.empty_like(x)
+    g = plan.graph(x, y)
+    for _ in range(5):
+        g.launch()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.launch()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e3)
+    g.close()
+    us = float(np.median(times))
+    out["impulse_256x128"] = {"us_per_application": us, "replays": 20,
+                              "value": x.numel() / (us * 1e-6) / 1e9, "unit": "Gpts/s",
+                              "note": "one level, 32768 points: launch-latency bound"}
+    w = synth.workload(3)
+    plan = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=w["nz"]), device=dev)
+    plan.tune(w["nvar"])
+    x = torch.from_numpy(w["x"]).to(dev)
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    for _ in range(warmup):
+        plan.apply(x, out=y)
+        plan.apply_adjoint(y, out=z)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.apply(x, out=y)
+        plan.apply_adjoint(y, out=z)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    npts = x.numel()
+    alg = 8 * npts + 33 * w["nx"] * w["ny"]
+    achieved = alg / (ms / 2 * 1e-3) / 1e9
+    out["global_1440x1080x75"] = {"value": 2 * npts / (ms * 1e-3) / 1e9, "unit": "Gpts/s",
+                                  "ms_per_step": ms, "points": npts,
+                                  "roofline": {"bound": "hbm", "achieved": achieved,
+                                               "peak": peak, "unit": "GB/s",
+                                               "frac": achieved / peak}}
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -378,9 +437,10 @@ def run_gpu(args):
                 "alg_bytes_per_application": alg_bytes,
                 "launches_per_application": launches / (2 * args.steps)}
 
-    ragged = None
+    ragged = configs = None
     if not args.no_ragged and world == 1:
         ragged = run_ragged(torch, dev, max(3, min(args.steps, 10)), max(args.warmup, 3))
+        configs = run_configs(torch, dev, max(3, min(args.steps, 10)), max(args.warmup, 3), peak)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -399,6 +459,7 @@ def run_gpu(args):
                   "ms_fwd": float(np.mean(f1)), "ms_adj": float(np.mean(a1))},
         "speedup_rf3_over_rf1x5": value / value1,
         "ragged64": ragged,
+        "configs": configs,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": "Gpts/s",
                 "h2d_bytes_per_step": 2 * 4 * npts, "d2h_bytes_per_step": 2 * 4 * npts},

@@ -128,3 +128,30 @@ def ragged_domains(n: int = 64, *, wid: int = 5, scale: float = 1.0,
         L = length_field(rng, ny, nx, 4.0 * blur, 3.0, 40.0)
         doms.append(dict(nx=nx, ny=ny, nz=nz, mask=mask, Lx=L, Ly=L.copy()))
     return doms
+
+
+def observations(w: dict, nobs: int = 50_000, *, wid: int = 4, sd: float = 0.5) -> dict:
+    """Seeded observation set for the 3D-VAR cost of workload `w`: each
+    observation draws a variable and a level uniformly and a continuous
+    position (x, y) uniformly, redrawn until the four grid points around it
+    are sea; its value is N(0, sd^2).  Returns var, lev (int64), x, y
+    (float64 grid coordinates) and value (float32)."""
+    rng = rng_for(wid)
+    mask = np.asarray(w["mask"]).astype(bool)
+    ny, nx = mask.shape[-2:]
+    var = rng.integers(0, w["nvar"], nobs)
+    lev = rng.integers(0, w["nz"], nobs)
+    xs = np.empty(nobs)
+    ys = np.empty(nobs)
+    todo = np.arange(nobs)
+    while todo.size:
+        x = rng.uniform(0.0, nx - 1.0, todo.size)
+        y = rng.uniform(0.0, ny - 1.0, todo.size)
+        i = np.minimum(x.astype(np.int64), nx - 2)
+        j = np.minimum(y.astype(np.int64), ny - 2)
+        ok = mask[j, i] & mask[j, i + 1] & mask[j + 1, i] & mask[j + 1, i + 1]
+        xs[todo[ok]] = x[ok]
+        ys[todo[ok]] = y[ok]
+        todo = todo[~ok]
+    value = rng.normal(0.0, sd, nobs).astype(np.float32)
+    return dict(var=var, lev=lev, x=xs, y=ys, value=value)
