@@ -59,6 +59,15 @@ enum {
     RF_NORM_UNIT_SUM = 1    /* every pass has DC gain 1 (the literal 1st-RF) */
 };
 
+/* rf_options.flags.  RF_FLAG_Q_CORRECTED (order 3 only, not the paper's
+ * filter): the Theorem 3.1 coefficients are taken at the scale q whose
+ * impulse-response variance, 2 (P1/P0) q + 2 ((P1/P0)^2 - 2 P2/P0) q^2, equals
+ * sigma^2, so the filter's variance is sigma^2 instead of about
+ * 3.10 sigma + 1.18 sigma^2; the normalisation stays that of sigma (DC gain
+ * sqrt(2 pi) sigma per direction).  The number of imaginary points still
+ * follows sigma. */
+enum { RF_FLAG_Q_CORRECTED = 1 };
+
 typedef struct rf_plan_ *rf_plan;
 typedef struct rf_graph_ *rf_graph;
 
@@ -76,7 +85,7 @@ typedef struct {
                              * sigma_coast); 0 = the bare heuristic ICs;
                              must be finite and >= 0                         */
     int norm;             /* RF_NORM_GAUSS_PEAK or RF_NORM_UNIT_SUM          */
-    int flags;            /* reserved, must be 0                             */
+    int flags;            /* 0 or RF_FLAG_Q_CORRECTED (order 3 only)         */
     int chunk;            /* reserved tuning override, 0 = automatic         */
     int tile;             /* reserved tuning override, 0 = automatic         */
 } rf_options;

@@ -45,13 +45,15 @@ def _load():
         lib = ctypes.CDLL(build())
         d, i, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
         vp = ctypes.c_void_p
-        lib.orc_rf3_coeffs.argtypes = [d, i, vp, vp, vp]
+        lib.orc_q_of_sigma.argtypes = [d]
+        lib.orc_q_of_sigma.restype = d
+        lib.orc_rf3_coeffs.argtypes = [d, i, i, vp, vp, vp]
         lib.orc_rf3_coeffs.restype = None
         lib.orc_rf1_coeffs.argtypes = [d, i, i, vp, vp]
         lib.orc_rf1_coeffs.restype = None
-        lib.orc_line.argtypes = [i, i, i, d, i, i64, vp, vp, vp, vp]
+        lib.orc_line.argtypes = [i, i, i, d, i, i, i64, vp, vp, vp, vp]
         lib.orc_line.restype = i
-        lib.orc_vh.argtypes = [i, i, i, d, i, i64, i64, i64, i64, vp, i64,
+        lib.orc_vh.argtypes = [i, i, i, d, i, i, i64, i64, i64, i64, vp, i64,
                                vp, vp, i64, vp, vp]
         lib.orc_vh.restype = i
         _lib = lib
@@ -62,13 +64,20 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def rf3_coeffs(sigma: float, norm: int = NORM_GAUSS_PEAK):
-    """Theorem 3.1 coefficients: returns (a[4], alpha[3], beta)."""
+def q_of_sigma(sigma: float) -> float:
+    """q of the q-corrected 3rd-RF: the filter of Theorem 3.1 taken at q has
+    impulse-response variance sigma^2."""
+    return float(_load().orc_q_of_sigma(float(sigma)))
+
+
+def rf3_coeffs(sigma: float, norm: int = NORM_GAUSS_PEAK, qcorr: bool = False):
+    """Theorem 3.1 coefficients: returns (a[4], alpha[3], beta); qcorr takes
+    the a_j at q(sigma) (beta still normalised with sigma)."""
     lib = _load()
     a = np.zeros(4)
     al = np.zeros(3)
     b = np.zeros(1)
-    lib.orc_rf3_coeffs(float(sigma), int(norm), _ptr(a), _ptr(al), _ptr(b))
+    lib.orc_rf3_coeffs(float(sigma), int(norm), int(bool(qcorr)), _ptr(a), _ptr(al), _ptr(b))
     return a, al, float(b[0])
 
 
@@ -83,7 +92,7 @@ def rf1_coeffs(sigma: float, K: int, norm: int = NORM_GAUSS_PEAK):
 
 def line(x, sigma, mask=None, *, order: int = 3, iters: int = 1,
          adjoint: bool = False, img_factor: float = 3.0,
-         norm: int = NORM_GAUSS_PEAK) -> np.ndarray:
+         norm: int = NORM_GAUSS_PEAK, qcorr: bool = False) -> np.ndarray:
     """Apply one 1-D filter G (or G^T) to the line x."""
     lib = _load()
     x = np.ascontiguousarray(x, dtype=np.float64)
@@ -92,7 +101,7 @@ def line(x, sigma, mask=None, *, order: int = 3, iters: int = 1,
     m = (np.ones(n, np.uint8) if mask is None
          else np.ascontiguousarray(mask, dtype=np.uint8))
     out = np.zeros(n)
-    rc = lib.orc_line(order, iters, int(adjoint), float(img_factor), norm, n,
+    rc = lib.orc_line(order, iters, int(adjoint), float(img_factor), norm, int(bool(qcorr)), n,
                       _ptr(m), _ptr(sig), _ptr(x), _ptr(out))
     if rc != 0:
         raise ValueError(f"orc_line failed with code {rc}")
@@ -101,7 +110,7 @@ def line(x, sigma, mask=None, *, order: int = 3, iters: int = 1,
 
 def vh(field, mask, Lx, Ly, *, order: int = 3, iters: int = 1,
        adjoint: bool = False, img_factor: float = 3.0,
-       norm: int = NORM_GAUSS_PEAK) -> np.ndarray:
+       norm: int = NORM_GAUSS_PEAK, qcorr: bool = False) -> np.ndarray:
     """V_H = G_y G_x (adjoint: G_x^T G_y^T) on a field [nvar][nz][ny][nx].
 
     field may also be [nz][ny][nx] or [ny][nx]; mask is [mask_nz][ny][nx]
@@ -125,7 +134,7 @@ def vh(field, mask, Lx, Ly, *, order: int = 3, iters: int = 1,
     lx = lev(Lx, np.float64)
     ly = lev(Ly, np.float64)
     out = np.zeros_like(f)
-    rc = lib.orc_vh(order, iters, int(adjoint), float(img_factor), norm,
+    rc = lib.orc_vh(order, iters, int(adjoint), float(img_factor), norm, int(bool(qcorr)),
                     nx, ny, nz, nvar, _ptr(m), m.shape[0], _ptr(lx), _ptr(ly),
                     lx.shape[0], _ptr(f), _ptr(out))
     if rc != 0:

@@ -15,6 +15,11 @@
  *  - 3rd-RF coefficients, Theorem 3.1: a_{i,0..3} from sigma_i = R_i/dx_i,
  *    alpha_{i,j} = a_{i,j}/a_{i,0}, beta_i = (2 pi sigma_i^2)^(1/4)
  *    (1 - sum_j alpha_{i,j}).
+ *  - Optional q-corrected 3rd-RF (not in the paper): the a_{i,j} are taken at
+ *    q_i instead of sigma_i, q_i the positive root of the impulse-response
+ *    variance of Theorem 3.1's filter, 2[(P1/P0) q + ((P1/P0)^2 - 2 P2/P0) q^2],
+ *    set equal to sigma_i^2, so the filter's variance is sigma_i^2; beta keeps
+ *    the normalisation of sigma_i.
  *  - 1st-RF coefficients, Sec. 3.1 (Hayden relation, Eq. "crucial"):
  *    E = K dx^2/R^2, alpha = 1 + E - sqrt(E(E+2)), beta = 1 - alpha, times
  *    the Gaussian-peak factor (2 pi sigma^2)^(1/(4K)) per pass unless the
@@ -54,11 +59,23 @@
 
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
 
-/* Theorem 3.1: a_{i,0..3}, alpha_{i,1..3} and beta_i for one grid point. */
-void orc_rf3_coeffs(double sigma, int norm, double a[4], double alpha[3],
+/* The q of the q-corrected 3rd-RF: variance(q) = A q^2 + B q = sigma^2 with
+ * A = 2 ((P1/P0)^2 - 2 P2/P0), B = 2 P1/P0, solved as 2 sigma^2 / (B + root)
+ * (no cancellation at small sigma). */
+double orc_q_of_sigma(double sigma)
+{
+    double r1 = 5.788982 / 3.738128, r2 = 3.382473 / 3.738128;
+    double A = 2.0 * (r1 * r1 - 2.0 * r2), B = 2.0 * r1;
+    double s2 = sigma * sigma;
+    return 2.0 * s2 / (B + sqrt(B * B + 4.0 * A * s2));
+}
+
+/* Theorem 3.1: a_{i,0..3}, alpha_{i,1..3} and beta_i for one grid point
+ * (qcorr: the a_{i,j} at q(sigma), beta still normalised with sigma). */
+void orc_rf3_coeffs(double sigma, int norm, int qcorr, double a[4], double alpha[3],
                     double *beta)
 {
-    double s = sigma, s2 = s * s, s3 = s2 * s;
+    double s = qcorr ? orc_q_of_sigma(sigma) : sigma, s2 = s * s, s3 = s2 * s;
     a[0] = 3.738128 + 5.788982 * s + 3.382473 * s2 + 1.000000 * s3;
     a[1] = 5.788982 * s + 6.764946 * s2 + 3.000000 * s3;
     a[2] = -3.382473 * s2 - 3.000000 * s3;
@@ -66,7 +83,7 @@ void orc_rf3_coeffs(double sigma, int norm, double a[4], double alpha[3],
     alpha[0] = a[1] / a[0];
     alpha[1] = a[2] / a[0];
     alpha[2] = a[3] / a[0];
-    double g = (norm == 1) ? 1.0 : pow(2.0 * ORC_PI * s2, 0.25);
+    double g = (norm == 1) ? 1.0 : pow(2.0 * ORC_PI * sigma * sigma, 0.25);
     *beta = g * (1.0 - (alpha[0] + alpha[1] + alpha[2]));
 }
 
@@ -118,7 +135,7 @@ static int64_t n_imaginary(double img_factor, double sigma_coast)
 
 /* Coefficients of the extended segment: imaginary points take the
  * coefficients of the adjacent coastal sea point. */
-static void fill_coeffs(int order, int K, int norm, const double *sig,
+static void fill_coeffs(int order, int K, int norm, int qcorr, const double *sig,
                         int64_t L, int64_t nl, int64_t nr, orc_ws *w)
 {
     int64_t m = nl + L + nr;
@@ -127,7 +144,7 @@ static void fill_coeffs(int order, int K, int norm, const double *sig,
         double *al = w->alpha + 3 * r;
         if (order == 3) {
             double a[4];
-            orc_rf3_coeffs(sig[src], norm, a, al, &w->beta[r]);
+            orc_rf3_coeffs(sig[src], norm, qcorr, a, al, &w->beta[r]);
         } else {
             orc_rf1_coeffs(sig[src], K, norm, &al[0], &w->beta[r]);
             al[1] = 0.0;
@@ -180,7 +197,7 @@ static void forward_backward_adjoint(int64_t m, const double *alpha,
 
 /* One line of n points.  mask[i] != 0 marks sea.  sig[i] = R_i/dx_i. */
 static int line_apply(int order, int iters, int adjoint, double img_factor,
-                      int norm, int64_t n, const uint8_t *mask,
+                      int norm, int qcorr, int64_t n, const uint8_t *mask,
                       const double *sig, const double *in, double *out,
                       orc_ws *w)
 {
@@ -196,7 +213,7 @@ static int line_apply(int order, int iters, int adjoint, double img_factor,
         int64_t nr = n_imaginary(img_factor, sig[i - 1]);
         int64_t m = nl + L + nr;
         if (ws_reserve(w, m) != ORC_OK) return ORC_ENOMEM;
-        fill_coeffs(order, iters, norm, sig + b, L, nl, nr, w);
+        fill_coeffs(order, iters, norm, qcorr, sig + b, L, nl, nr, w);
         for (int64_t t = 0; t < L; ++t) out[b + t] = in[b + t];
         for (int k = 0; k < iters; ++k) {
             /* extend with zeros (E, or R^T for the adjoint) */
@@ -213,9 +230,10 @@ static int line_apply(int order, int iters, int adjoint, double img_factor,
     return ORC_OK;
 }
 
-static int check_opts(int order, int iters)
+static int check_opts(int order, int iters, int qcorr)
 {
     if (order != 1 && order != 3) return ORC_EINVAL;
+    if (qcorr && order != 3) return ORC_EINVAL;
     if (iters < 1) return ORC_EINVAL;
     if (order == 3 && iters != 1) return ORC_EINVAL;
     return ORC_OK;
@@ -223,12 +241,12 @@ static int check_opts(int order, int iters)
 
 /* Public: one 1-D line (the operator G of one direction). */
 int orc_line(int order, int iters, int adjoint, double img_factor, int norm,
-             int64_t n, const uint8_t *mask, const double *sig,
+             int qcorr, int64_t n, const uint8_t *mask, const double *sig,
              const double *in, double *out)
 {
-    if (check_opts(order, iters) != ORC_OK || n < 0) return ORC_EINVAL;
+    if (check_opts(order, iters, qcorr) != ORC_OK || n < 0) return ORC_EINVAL;
     orc_ws w = {0};
-    int rc = line_apply(order, iters, adjoint, img_factor, norm, n, mask, sig,
+    int rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr, n, mask, sig,
                         in, out, &w);
     ws_free(&w);
     return rc;
@@ -239,11 +257,11 @@ int orc_line(int order, int iters, int adjoint, double img_factor, int norm,
  * [L_nz][ny][nx] in grid units; mask_nz and L_nz are 1 (shared by every
  * level) or nz.  in and out may not alias. */
 int orc_vh(int order, int iters, int adjoint, double img_factor, int norm,
-           int64_t nx, int64_t ny, int64_t nz, int64_t nvar,
+           int qcorr, int64_t nx, int64_t ny, int64_t nz, int64_t nvar,
            const uint8_t *mask, int64_t mask_nz, const double *Lx,
            const double *Ly, int64_t L_nz, const double *in, double *out)
 {
-    if (check_opts(order, iters) != ORC_OK) return ORC_EINVAL;
+    if (check_opts(order, iters, qcorr) != ORC_OK) return ORC_EINVAL;
     if (nx < 0 || ny < 0 || nz < 0 || nvar < 0) return ORC_EINVAL;
     if (!(mask_nz == 1 || mask_nz == nz) || !(L_nz == 1 || L_nz == nz))
         return ORC_EINVAL;
@@ -269,7 +287,7 @@ int orc_vh(int order, int iters, int adjoint, double img_factor, int norm,
                 double *b = pass == 0 ? tmp : dst;
                 if (along_x) {
                     for (int64_t j = 0; j < ny && rc == ORC_OK; ++j)
-                        rc = line_apply(order, iters, adjoint, img_factor, norm,
+                        rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr,
                                         nx, mk + j * nx, sx + j * nx,
                                         a + j * nx, b + j * nx, &w);
                 } else {
@@ -279,7 +297,7 @@ int orc_vh(int order, int iters, int adjoint, double img_factor, int norm,
                             ls[j] = sy[j * nx + i];
                             li[j] = a[j * nx + i];
                         }
-                        rc = line_apply(order, iters, adjoint, img_factor, norm,
+                        rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr,
                                         ny, lm, ls, li, lo, &w);
                         for (int64_t j = 0; j < ny; ++j) b[j * nx + i] = lo[j];
                     }

@@ -15,6 +15,13 @@
 // and keeps FP32 rounding small when 1 - sum alpha is tiny (large sigma).
 // First-order filter (Sec. 3.1, Hayden): E = K/sigma^2, e = 1 - alpha =
 // sqrt(E(E+2)) - E, and the step is p_i = p_{i-1} + (beta s_i - e p_{i-1}).
+//
+// q-corrected third-order filter (an option, not the paper's filter): the
+// impulse response of the Theorem 3.1 filter at scale s has variance
+// 2 (P1/P0) s + 2 ((P1/P0)^2 - 2 P2/P0) s^2 (the first two cumulants of
+// 1/D(s(1 - e^t)), D the cubic of Appendix A), not s^2.  Taking the a_j at the
+// positive root q of variance(q) = sigma^2 gives variance sigma^2; beta keeps
+// the normalisation of sigma, so the DC gain stays sqrt(2 pi) sigma.
 #pragma once
 #include <cstdint>
 
@@ -30,20 +37,30 @@ struct Coef64 {
     double beta, e, c1, c2;
 };
 
+// Scale q with variance(q) = sigma^2, as 2 sigma^2 / (B + sqrt(B^2 + 4 A
+// sigma^2)) for A q^2 + B q = sigma^2 (no cancellation at small sigma).
+__host__ __device__ inline double q_corrected(double sigma)
+{
+    const double r1 = kP1 / kP0, r2 = kP2 / kP0;
+    const double A = 2.0 * (r1 * r1 - 2.0 * r2), Bq = 2.0 * r1;
+    const double s2 = sigma * sigma;
+    return 2.0 * s2 / (Bq + sqrt(Bq * Bq + 4.0 * A * s2));
+}
+
 // Per-point coefficients in FP64 (sigma > 0, finite).  norm: 0 Gaussian peak,
-// 1 unit sum.  For order 1, c1 = c2 = 0.
+// 1 unit sum.  qc: q-corrected third-order filter.  For order 1, c1 = c2 = 0.
 __host__ __device__ inline Coef64 coef_fp64(double sigma, int order, int K,
-                                            int norm)
+                                            int norm, bool qc = false)
 {
     Coef64 c;
     if (order == 3) {
-        double s = sigma;
+        double s = qc ? q_corrected(sigma) : sigma;
         double a0 = kP0 + s * (kP1 + s * (kP2 + s));
         double inv = 1.0 / a0;
         c.e = kP0 * inv;
         c.c1 = (kP0 + kP1 * s) * inv;
         c.c2 = (kP0 + s * (kP1 + kP2 * s)) * inv;
-        double g = norm == 1 ? 1.0 : sqrt(sqrt(kTwoPi) * s);
+        double g = norm == 1 ? 1.0 : sqrt(sqrt(kTwoPi) * sigma);
         c.beta = g * c.e;
     } else {
         double E = (double)K / (sigma * sigma);
@@ -66,9 +83,9 @@ __host__ __device__ inline Coef64 coef_fp64(double sigma, int order, int K,
 //   M = sum_{k=1..n} A^{k-1} b c^T A^k.
 // Order 3 writes the 3x3 M row-major into m[0..9); order 1 writes m[0].
 __host__ __device__ inline void tail_map_fp64(double sigma, int n_img, int order,
-                                              int K, int norm, double *m)
+                                              int K, int norm, bool qc, double *m)
 {
-    Coef64 c = coef_fp64(sigma, order, K, norm);
+    Coef64 c = coef_fp64(sigma, order, K, norm, qc);
     if (order == 1) {
         double a = 1.0 - c.e, acc = 0.0, v = c.beta, w = a;
         for (int k = 1; k <= n_img; ++k) {

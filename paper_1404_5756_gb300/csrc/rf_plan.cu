@@ -157,7 +157,8 @@ rf_status check_options(const rf_options &o)
     if (o.iters < 1 || (o.order == 3 && o.iters != 1)) return RF_EINVAL;
     if (!(o.img_factor >= 0.0) || !std::isfinite(o.img_factor)) return RF_EINVAL;
     if (o.norm != RF_NORM_GAUSS_PEAK && o.norm != RF_NORM_UNIT_SUM) return RF_EINVAL;
-    if (o.flags != 0 || o.chunk < 0 || o.tile < 0) return RF_EINVAL;
+    if ((o.flags & ~RF_FLAG_Q_CORRECTED) != 0 || o.chunk < 0 || o.tile < 0) return RF_EINVAL;
+    if ((o.flags & RF_FLAG_Q_CORRECTED) && o.order != 3) return RF_EINVAL;
     return RF_OK;
 }
 
@@ -192,7 +193,7 @@ rf_status cuda_status(cudaError_t e)
 __global__ void coef_lines_kernel(int64_t ncl, int64_t nx, int64_t ny, int along_y,
                                   const uint8_t *__restrict__ mask, int64_t mask_nz,
                                   const float *__restrict__ L, int64_t L_nz, int order,
-                                  int K, int norm, float4 *__restrict__ out)
+                                  int K, int norm, int qc, float4 *__restrict__ out)
 {
     const int64_t plane = nx * ny;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -206,7 +207,7 @@ __global__ void coef_lines_kernel(int64_t ncl, int64_t nx, int64_t ny, int along
     float4 c = make_float4(0.f, 0.f, 0.f, -1.f);
     if (m[p]) {
         const double s = (double)L[(L_nz > 1 ? lev : 0) * plane + p];
-        const Coef64 k = coef_fp64(s, order, K, norm);
+        const Coef64 k = coef_fp64(s, order, K, norm, qc != 0);
         c = make_float4((float)k.beta, -(float)k.e, -(float)k.c1, -(float)k.c2);
         const int64_t pn = along_y ? p + nx : p + 1;
         if (pos == n - 1 || !m[pn]) c.x = -c.x;
@@ -217,12 +218,12 @@ __global__ void coef_lines_kernel(int64_t ncl, int64_t nx, int64_t ny, int along
 // Boundary maps in FP64, stored as hi/lo FP32 pairs (hi = m rounded to
 // FP32, lo = the rest rounded to FP32) for the compensated FP32 application.
 __global__ void tail_kernel(int64_t n, const TailSpec *__restrict__ spec,
-                            float2 *__restrict__ tmap, int order, int K, int norm)
+                            float2 *__restrict__ tmap, int order, int K, int norm, int qc)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double m[9];
-    tail_map_fp64((double)spec[i].sigma, spec[i].n_img, order, K, norm, m);
+    tail_map_fp64((double)spec[i].sigma, spec[i].n_img, order, K, norm, qc != 0, m);
     for (int r = 0; r < 9; ++r) {
         const float hi = (float)m[r];
         tmap[9 * i + r] = make_float2(hi, (float)(m[r] - (double)hi));
@@ -427,6 +428,7 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
     choose_chunk(q);
     const int64_t plane = g.nx * g.ny, ncl = D.ncl;
     const int o = P->opt.order, K = P->opt.iters, nm = P->opt.norm;
+    const int qc = (P->opt.flags & RF_FLAG_Q_CORRECTED) ? 1 : 0;
     const int XS = o == 3 ? 36 : 4;
 
     RF_TRY(dev_alloc(&q.coef, ncl * plane, &P->bytes));
@@ -445,7 +447,7 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
                                        cudaMemcpyHostToDevice, st)));
     const int64_t npts = ncl * plane;
     coef_lines_kernel<<<(unsigned)((npts + 255) / 256), 256, 0, st>>>(
-        ncl, g.nx, g.ny, dir, mask_dev, g.mask_nz, L_dev, g.L_nz, o, K, nm, q.coef);
+        ncl, g.nx, g.ny, dir, mask_dev, g.mask_nz, L_dev, g.L_nz, o, K, nm, qc, q.coef);
     RF_TRY(cuda_status(cudaGetLastError()));
     if (q.R > 0) {
         const int64_t nrec = ncl * q.nlines * 32;
@@ -465,7 +467,7 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
                                                   cudaMemcpyHostToDevice, st));
         if (s == RF_OK) {
             tail_kernel<<<(unsigned)((q.ntail + 127) / 128), 128, 0, st>>>(q.ntail, dsp, q.tmap,
-                                                                           o, K, nm);
+                                                                           o, K, nm, qc);
             s = cuda_status(cudaGetLastError());
         }
         if (s == RF_OK) s = cuda_status(cudaStreamSynchronize(st));

@@ -24,11 +24,13 @@ class Options:
     iters: int = 1          # K (1 for order 3)
     img_factor: float = 3.0
     norm: int = _lib.RF_NORM_GAUSS_PEAK
+    qcorr: bool = False     # q-corrected 3rd-RF: impulse variance sigma^2
 
     def to_c(self) -> _lib.rf_options:
         o = _lib.rf_options_default()
         o.order, o.iters = int(self.order), int(self.iters)
         o.img_factor, o.norm = float(self.img_factor), int(self.norm)
+        o.flags = _lib.RF_FLAG_Q_CORRECTED if self.qcorr else 0
         return o
 
 

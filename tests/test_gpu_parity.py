@@ -135,6 +135,31 @@ def test_options_img_factor_and_norm(cfg2_small, img, norm):
         assert rel_err(g, o) <= TOL
 
 
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("img,norm", [(3.0, 0), (0.0, 1)])
+def test_q_corrected_filter(cfg2_small, cfg1, adjoint, img, norm):
+    """The q-corrected 3rd-RF (an option, not the paper's filter) against the
+    oracle's, on the coastal regional grid and the impulse grid."""
+    for w in (cfg2_small, cfg1):
+        x = np.ascontiguousarray(w["x"][:, :1])
+        plan = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=1),
+                    Options(img_factor=img, norm=norm, qcorr=True))
+        xt = torch.from_numpy(x).cuda()
+        g = (plan.apply_adjoint(xt) if adjoint else plan.apply(xt)).cpu().numpy()
+        o = orc.vh(x.astype(np.float64), w["mask"], np.asarray(w["Lx"], np.float64),
+                   np.asarray(w["Ly"], np.float64), adjoint=adjoint, img_factor=img,
+                   norm=norm, qcorr=True)
+        assert rel_err(g, o) <= TOL
+        assert plan.status() == 0
+
+
+def test_q_correction_needs_the_third_order_filter(cfg1):
+    w = cfg1
+    with pytest.raises(Exception):
+        Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=1),
+             Options(order=1, iters=5, qcorr=True))
+
+
 def test_all_land_and_all_sea():
     ny, nx = 20, 24
     L = np.full((ny, nx), 3.0, np.float32)

@@ -124,6 +124,47 @@ def test_rf1_hayden_variance_and_gain(sigma, K):
     assert hg.sum() == pytest.approx(np.sqrt(2 * np.pi) * sigma, rel=1e-11)
 
 
+@pytest.mark.parametrize("sigma", [0.7, 2.0, 5.0, 10.0, 40.0])
+def test_q_corrected_rf3_has_variance_sigma_squared(sigma):
+    """The q-corrected 3rd-RF (an option, not the paper's filter)
+    takes the Theorem 3.1 coefficients at q(sigma) so that the measured
+    variance of the line filter's impulse response is sigma^2, while the
+    normalisation of sigma keeps the response sum at sqrt(2 pi) sigma."""
+    n = int(40 * sigma) + 40
+    x = np.zeros(2 * n + 1)
+    x[n] = 1.0
+    h = orc.line(x, sigma, img_factor=0.0, qcorr=True)
+    k = np.arange(-n, n + 1)
+    m0 = h.sum()
+    assert m0 == pytest.approx(np.sqrt(2 * np.pi) * sigma, rel=1e-11)
+    assert abs((k * h).sum() / m0) < 1e-9 * sigma
+    assert (k * k * h).sum() / m0 == pytest.approx(sigma**2, rel=1e-9)
+    q = orc.q_of_sigma(sigma)
+    assert 0.0 < q < sigma   # the plain filter is wider than sigma
+    _, _, beta = orc.rf3_coeffs(sigma, qcorr=True)
+    _, _, beta_q = orc.rf3_coeffs(q)
+    # beta: the recursion of q with the normalisation of sigma
+    assert beta == pytest.approx(beta_q * np.sqrt(sigma / q), rel=1e-12)
+
+
+def test_q_corrected_rf3_fits_the_gaussian_better_at_small_sigma():
+    """Relative L2 distance of the impulse response to exp(-x^2/2 sigma^2):
+    the variance match helps where the plain filter is much too wide (small
+    sigma) and costs at large sigma, where the responses' heavier tails carry
+    the extra variance."""
+    def l2(sigma, qcorr):
+        n = int(40 * sigma) + 40
+        x = np.zeros(2 * n + 1)
+        x[n] = 1.0
+        h = orc.line(x, sigma, img_factor=0.0, qcorr=qcorr)
+        k = np.arange(-n, n + 1)
+        g = np.exp(-k * k / (2 * sigma * sigma))
+        return np.sqrt(((h - g) ** 2).sum() / (g * g).sum())
+    assert l2(2.0, True) < 0.5 * l2(2.0, False)
+    assert l2(5.0, True) < l2(5.0, False)
+    assert l2(40.0, True) > l2(40.0, False)
+
+
 def test_rf1_coefficients_satisfy_hayden():
     for sigma, K in [(1.5, 1), (5.0, 5), (40.0, 10)]:
         alpha, beta = orc.rf1_coeffs(sigma, K, orc.NORM_UNIT_SUM)
@@ -400,6 +441,8 @@ def test_invalid_inputs_rejected():
         orc.line(np.ones(5), np.nan)
     with pytest.raises(ValueError):
         orc.line(np.ones(5), 2.0, order=3, iters=2)
+    with pytest.raises(ValueError):
+        orc.line(np.ones(5), 2.0, order=1, iters=5, qcorr=True)
     # land points may carry any length scale
     mask = np.array([1, 0, 1, 1, 0], np.uint8)
     sig = np.array([2.0, -5.0, 2.0, 3.0, np.nan])
