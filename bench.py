@@ -354,6 +354,58 @@ def run_configs(torch, dev, steps, warmup, peak):
     return out
 
 
+def run_cg(torch, dev, w, plan):
+    """Conjugate gradients on the system of Eq. "eight" (control-variable
+    form, B = V_H V_H^T) for the regional grid with 50,000 seeded
+    observations, bilinear H, R = 0.5^2 I; each iteration is one CUDA-graph
+    replay of V_H, H, R^-1, H^T, V_H^T and the CG updates.  The time per
+    iteration is (t(30 iterations) - t(5 iterations)) / 25, which cancels the
+    set-up and capture."""
+    from paper_1404_5756_gb300 import synth
+    from paper_1404_5756_gb300.var3d import Var3D
+    obs = synth.observations(w)
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    i0 = np.minimum(np.floor(obs["x"]).astype(np.int64), nx - 2)
+    j0 = np.minimum(np.floor(obs["y"]).astype(np.int64), ny - 2)
+    fx, fy = obs["x"] - i0, obs["y"] - j0
+    base = (obs["var"] * nz + obs["lev"]) * ny * nx
+    idx = torch.from_numpy(np.stack([base + j0 * nx + i0, base + j0 * nx + i0 + 1,
+                                     base + (j0 + 1) * nx + i0,
+                                     base + (j0 + 1) * nx + i0 + 1])).to(dev)
+    wts = torch.from_numpy(np.stack([(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy,
+                                     fx * fy]).astype(np.float32)).to(dev)
+    shape = w["x"].shape
+    n = int(np.prod(shape))
+
+    def H(u):
+        return (u.reshape(-1)[idx] * wts).sum(0)
+
+    def Ht(r):
+        out = torch.zeros(n, device=dev, dtype=r.dtype)
+        out.index_add_(0, idx.reshape(-1), (wts * r).reshape(-1))
+        return out.reshape(shape)
+
+    d = torch.from_numpy(obs["value"]).to(dev)
+    prob = Var3D(plan, H, Ht, torch.full_like(d, 4.0), d, shape)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(iters):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prob.solve(iters)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    timed(5)
+    ms = (timed(30) - timed(5)) / 25
+    return {"ms_per_iteration": ms, "iterations_per_s": 1e3 / ms,
+            "vh_applications_per_iteration": 2,
+            "value": 2 * n / (ms * 1e-3) / 1e9, "unit": "Gpts/s (V_H applications)",
+            "observations": len(obs["value"]), "graph": True}
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -452,6 +504,7 @@ def run_gpu(args):
     if not args.no_ragged and world == 1:
         ragged = run_ragged(torch, dev, max(3, min(args.steps, 10)), max(args.warmup, 3))
         configs = run_configs(torch, dev, max(3, min(args.steps, 10)), max(args.warmup, 3), peak)
+        configs["cg_regional_50k_obs"] = run_cg(torch, dev, w, plan3)
 
     cpu = None
     if not args.no_cpu_baseline:
