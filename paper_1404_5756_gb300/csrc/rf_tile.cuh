@@ -443,8 +443,36 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     auto group_size = [&](int64_t gi) {
         return (int)min((int64_t)B, one_level ? nitems - gi * B : nvar - gi * B);
     };
+    // rows in slice pairs with one buffer: 16-byte loads from both slices of
+    // a pair, interleaved in registers into two 16-byte shared stores (the
+    // copy engine cannot interleave); otherwise element-wise cp.async
+    const bool pv = W == 2 && a.vec4 && a.nbuf == 1;
     auto issue_loads = [&](int64_t gi, int buf) {
         const int nb = group_size(gi);
+        if (pv) {
+            for (int u = 0; u < (nb + 1) / 2; ++u) {
+                const float *s0 = a.in + slice_of(gi, 2 * u) * a.plane;
+                const float *s1 = 2 * u + 1 < nb ? a.in + slice_of(gi, 2 * u + 1) * a.plane : nullptr;
+                float *db = ds + (int64_t)buf * B * R * ss + (int64_t)u * 2 * R * ss;
+                for (int r = 0; r < lines_here; ++r) {
+                    const float4 *g0 = reinterpret_cast<const float4 *>(s0 + (line0 + r) * a.line_stride);
+                    const float4 *g1 = s1 ? reinterpret_cast<const float4 *>(s1 + (line0 + r) * a.line_stride)
+                                          : nullptr;
+                    float4 *sr = reinterpret_cast<float4 *>(db + 2 * r * ss);
+#pragma unroll 4
+                    for (int q = threadIdx.x; q < n / 4; q += blockDim.x) {
+                        const float4 x0 = __ldg(g0 + q);
+                        const float4 x1 = g1 ? __ldg(g1 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        sr[2 * q] = make_float4(x0.x, x1.x, x0.y, x1.y);
+                        sr[2 * q + 1] = make_float4(x0.z, x1.z, x0.w, x1.w);
+                    }
+                }
+            }
+            // the boundary-map copies issued earlier join a group, so the
+            // wait before filtering covers them
+            asm volatile("cp.async.commit_group;\n" ::);
+            return;
+        }
         for (int b = 0; b < nb; ++b) {
             const float *src = a.in + slice_of(gi, b) * a.plane;
             float *db = ds + (int64_t)buf * B * R * ss + (b / W) * W * R * ss + b % W;
@@ -546,7 +574,25 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
         }
         __syncthreads();
         // ---- store
-        for (int b = 0; b < nb; ++b) {
+        if (pv) {
+            for (int u = 0; u < (nb + 1) / 2; ++u) {
+                float *d0 = a.out + slice_of(gi, 2 * u) * a.plane;
+                float *d1 = 2 * u + 1 < nb ? a.out + slice_of(gi, 2 * u + 1) * a.plane : nullptr;
+                const float *db = ds + (int64_t)buf * B * R * ss + (int64_t)u * 2 * R * ss;
+                for (int r = 0; r < lines_here; ++r) {
+                    float4 *g0 = reinterpret_cast<float4 *>(d0 + (line0 + r) * a.line_stride);
+                    float4 *g1 = d1 ? reinterpret_cast<float4 *>(d1 + (line0 + r) * a.line_stride) : nullptr;
+                    const float4 *sr = reinterpret_cast<const float4 *>(db + 2 * r * ss);
+#pragma unroll 4
+                    for (int q = threadIdx.x; q < n / 4; q += blockDim.x) {
+                        const float4 y0 = sr[2 * q], y1 = sr[2 * q + 1];
+                        g0[q] = make_float4(y0.x, y0.z, y1.x, y1.z);
+                        if (g1) g1[q] = make_float4(y0.y, y0.w, y1.y, y1.w);
+                    }
+                }
+            }
+        }
+        for (int b = 0; b < (pv ? 0 : nb); ++b) {
             float *dst = a.out + slice_of(gi, b) * a.plane;
             const float *db = ds + (int64_t)buf * B * R * ss + (b / W) * W * R * ss + b % W;
             if (a.pt_stride == 1) {
