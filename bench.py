@@ -467,6 +467,7 @@ def run_gpu(args):
     plan_q.close()
 
     # ---- end to end through the C ABI on pinned host buffers
+    bound = bind_to_gpu_numa_node(torch, dev)
     xh = torch.from_numpy(w["x"]).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     zh = torch.empty_like(xh).pin_memory()
@@ -528,7 +529,8 @@ def run_gpu(args):
         "configs": configs,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": "Gpts/s",
-                "h2d_bytes_per_step": 2 * 4 * npts, "d2h_bytes_per_step": 2 * 4 * npts},
+                "h2d_bytes_per_step": 2 * 4 * npts, "d2h_bytes_per_step": 2 * 4 * npts,
+                "host_cpus": f"{bound[0]}-{bound[-1]} ({len(bound)})" if bound else "unbound"},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -536,6 +538,31 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bind_to_gpu_numa_node(torch, dev):
+    """Run on the CPUs next to the GPU, so the pinned host buffers of the
+    end-to-end measurement are placed on its NUMA node (first touch) rather
+    than wherever the process happened to start.  No-op where the topology
+    cannot be read."""
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        bus = subprocess.run(["nvidia-smi", "-i", uuid, "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=20).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest.lower()}/local_cpulist"
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return sorted(cpus)
+    except Exception:
+        pass
+    return None
 
 
 def max_over_ranks(torch, world, v):
