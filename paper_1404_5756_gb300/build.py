@@ -1,4 +1,8 @@
-"""Build librfvh.so (the CUDA C-ABI library) in-tree with nvcc for sm_103a."""
+"""Build librfvh.so (the CUDA C-ABI library) in-tree with nvcc for sm_103a.
+
+Every translation unit under csrc/ compiles to an object file in parallel
+(the tile kernels are split by filter order and direction for this), then
+nvcc links the shared library."""
 from __future__ import annotations
 
 import glob
@@ -11,8 +15,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "librfvh.so")
+OBJ = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def nvcc() -> str:
@@ -30,23 +36,33 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = (sources() + glob.glob(os.path.join(CSRC, "*.cuh"))
+    deps = (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__])
     return any(os.path.getmtime(f) > t for f in deps)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ into one shared library (one nvcc call;
-    the translation units compile in parallel with --threads)."""
+    """Compile every .cu under csrc/ (in parallel) and link one shared
+    library; a no-op when the library is newer than every source."""
     if not force and not _stale():
         return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--threads", "0",
-           "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
-           f"-I{INCLUDE}", f"-I{CSRC}", *sources(), "-o", tmp]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+    os.makedirs(OBJ, exist_ok=True)
+    tag = os.getpid()
+    procs, objs = [], []
+    for src in sources():
+        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + f".{tag}.o")
+        cmd = [nvcc(), *ARCH, *FLAGS, f"-I{INCLUDE}", f"-I{CSRC}", "-c", src, "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append((src, subprocess.Popen(cmd)))
+        objs.append(obj)
+    failed = [src for src, p in procs if p.wait() != 0]
+    if failed:
+        raise RuntimeError(f"nvcc failed on {', '.join(os.path.basename(f) for f in failed)}")
+    tmp = LIB + f".{tag}.tmp"
+    subprocess.check_call([nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp])
+    for obj in objs:
+        os.remove(obj)
     os.replace(tmp, LIB)
     return LIB
 

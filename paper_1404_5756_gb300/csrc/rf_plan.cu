@@ -14,6 +14,7 @@
 
 #include "rfvh.h"
 #include "rf_coef.cuh"
+#include "rf_launch.h"
 #include "rf_line.cuh"
 #include "rf_tile.cuh"
 
@@ -24,11 +25,6 @@ namespace {
 struct TailSpec {
     float sigma;
     int n_img;
-};
-
-// (lines per CTA, slices per thread) of a tile-kernel launch.
-struct TileShape {
-    int R, B;
 };
 
 // How one direction of one domain is launched for a given slice count.
@@ -406,12 +402,12 @@ void choose_chunk(Dir &q)
     q.R = q.C <= kMaxChunk ? 1 : 0;   // R > 0 marks "tile kernel usable"
 }
 
-// (lines per CTA, slices per thread) pairs the tile kernel is built for, in
-// order of preference.
+// (lines per CTA, slices per thread) pairs the tile kernel is built for
+// (rf_launch_impl.cuh), in order of preference.
 constexpr TileShape kShapesY[] = {{8, 4}, {8, 2}, {4, 4}, {8, 1}, {4, 2}, {2, 4},
-                                  {4, 1}, {2, 1}, {1, 4}, {1, 1}};
+                                  {4, 1}, {2, 1}, {1, 4}, {1, 1}, {1, 8}, {2, 8}};
 constexpr TileShape kShapesX[] = {{4, 4}, {8, 4}, {2, 4}, {4, 2}, {8, 2}, {4, 1},
-                                  {8, 1}, {1, 4}, {2, 1}, {1, 1}};
+                                  {8, 1}, {1, 4}, {2, 1}, {1, 1}, {1, 8}, {2, 8}};
 
 rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
                     const float *L_dev, const std::vector<int32_t> &base,
@@ -514,85 +510,6 @@ rf_status ensure(float **buf, int64_t *have, int64_t need, int64_t *bytes)
 }
 
 // ------------------------------------------------------------------ apply
-// Raise a kernel's dynamic shared-memory limit once per device and size, so
-// a launch inside a stream capture makes no attribute call.
-constexpr int kAttrDevices = 64;
-template <int ORDER, bool ADJ, int R, int B, bool MULTI>
-void smem_attr(size_t smem)
-{
-    static std::mutex mu;
-    static size_t done[kAttrDevices] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> lock(mu);
-    if (dev >= 0 && dev < kAttrDevices && smem <= done[dev]) return;
-    if (MULTI)
-        cudaFuncSetAttribute(tile_multi_kernel<ORDER, ADJ, R, B>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else
-        cudaFuncSetAttribute(tile_kernel<ORDER, ADJ, R, B>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (dev >= 0 && dev < kAttrDevices) done[dev] = smem;
-}
-
-template <int ORDER, bool ADJ, int R, int B>
-void launch_tile(const TileArgs &a, int64_t nlines, int64_t groups, size_t smem,
-                 cudaStream_t st)
-{
-    smem_attr<ORDER, ADJ, R, B, false>(smem);
-    dim3 grid((unsigned)((nlines + R - 1) / R), (unsigned)groups);
-    tile_kernel<ORDER, ADJ, R, B><<<grid, 32 * R, smem, st>>>(a);
-}
-
-template <int ORDER, bool ADJ>
-void launch_shape(const TileArgs &a, TileShape sh, int64_t nlines, int64_t groups,
-                  size_t smem, cudaStream_t st)
-{
-#define RF_SHAPE(r, b)                                                           \
-    if (sh.R == r && sh.B == b) {                                                \
-        launch_tile<ORDER, ADJ, r, b>(a, nlines, groups, smem, st);              \
-        return;                                                                  \
-    }
-    RF_SHAPE(8, 4) RF_SHAPE(8, 2) RF_SHAPE(8, 1) RF_SHAPE(4, 4) RF_SHAPE(4, 2)
-    RF_SHAPE(4, 1) RF_SHAPE(2, 4) RF_SHAPE(2, 1) RF_SHAPE(1, 4) RF_SHAPE(1, 1)
-#undef RF_SHAPE
-}
-
-// How one direction of one domain is launched for a given slice count.
-
-// Tile shape: a CTA's slices are the variables of one level when the
-// coefficients differ per level, else the slices are split for about two
-// waves of CTAs.
-template <int ORDER, bool ADJ, int R, int B, bool MULTI = false>
-int tile_occupancy(size_t smem)
-{
-    smem_attr<ORDER, ADJ, R, B, MULTI>(smem);
-    int blocks = 0;
-    cudaError_t e;
-    if (MULTI)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &blocks, tile_multi_kernel<ORDER, ADJ, R, B>, 32 * R, smem);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_kernel<ORDER, ADJ, R, B>,
-                                                          32 * R, smem);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return blocks;
-}
-
-template <int ORDER, bool ADJ, bool MULTI = false>
-int shape_occupancy(TileShape sh, size_t smem)
-{
-#define RF_SHAPE(r, b) \
-    if (sh.R == r && sh.B == b) return tile_occupancy<ORDER, ADJ, r, b, MULTI>(smem);
-    RF_SHAPE(8, 4) RF_SHAPE(8, 2) RF_SHAPE(8, 1) RF_SHAPE(4, 4) RF_SHAPE(4, 2)
-    RF_SHAPE(4, 1) RF_SHAPE(2, 4) RF_SHAPE(2, 1) RF_SHAPE(1, 4) RF_SHAPE(1, 1)
-#undef RF_SHAPE
-    return 0;
-}
-
 int num_sms()
 {
     static int sms = 0;
@@ -620,7 +537,7 @@ bool finish_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk, LaunchC
     if (q.R == 0 || (L.sh.B > 1 && L.sh.B > per_cta)) return false;
     L.smem = (size_t)tile_smem_bytes(L.sh.R, L.sh.B, smem_stride(q.n), q.max_re, L.nbuf);
     if (L.smem > kSmemMax) return false;
-    L.occ = shape_occupancy<ORDER, ADJ>(L.sh, L.smem);
+    L.occ = shape_occupancy<ORDER, ADJ, false>(L.sh, L.smem);
     if (L.occ < 1) return false;
     L.tile = true;
     if (D.ncl > 1) {
@@ -888,26 +805,6 @@ MultiCfg multi_cfg(rf_plan_ *p, int dir, int64_t nvar, bool adjoint)
         }
     p->mcfg.push_back(c);
     return c;
-}
-
-template <int ORDER, bool ADJ, int R, int B>
-void launch_multi_rb(const MultiArgs &m, unsigned grid, size_t smem, cudaStream_t st)
-{
-    smem_attr<ORDER, ADJ, R, B, true>(smem);
-    tile_multi_kernel<ORDER, ADJ, R, B><<<grid, 32 * R, smem, st>>>(m);
-}
-
-template <int ORDER, bool ADJ>
-void launch_multi(const MultiArgs &m, TileShape sh, unsigned grid, size_t smem, cudaStream_t st)
-{
-#define RF_SHAPE(r, b)                                                   \
-    if (sh.R == r && sh.B == b) {                                        \
-        launch_multi_rb<ORDER, ADJ, r, b>(m, grid, smem, st);            \
-        return;                                                          \
-    }
-    RF_SHAPE(8, 4) RF_SHAPE(8, 2) RF_SHAPE(8, 1) RF_SHAPE(4, 4) RF_SHAPE(4, 2)
-    RF_SHAPE(4, 1) RF_SHAPE(2, 4) RF_SHAPE(2, 1) RF_SHAPE(1, 4) RF_SHAPE(1, 1)
-#undef RF_SHAPE
 }
 
 // One pass (direction c.dir) over every tile-kernel domain: persistent
