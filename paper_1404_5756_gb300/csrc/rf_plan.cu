@@ -646,8 +646,10 @@ TileArgs tile_args(const Domain &D, const Dir &q, const float *in, float *out, i
     a.iters = iters;
     a.smem_stride = (int)smem_stride(q.n);
     a.max_re = q.ntail > 0 ? q.max_re : 0;
-    a.vec4 = q.pt_stride == 1 && q.n % 4 == 0 && ((uintptr_t)in % 16) == 0 &&
-             ((uintptr_t)out % 16) == 0;
+    // x pass: rows start 16-byte aligned; y pass: rows of the grid do (so
+    // groups of 4 adjacent columns can move as one 16-byte access)
+    const bool al = ((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0;
+    a.vec4 = al && (q.pt_stride == 1 ? q.n % 4 == 0 : q.pt_stride % 4 == 0);
     a.nbuf = nbuf;
     return a;
 }

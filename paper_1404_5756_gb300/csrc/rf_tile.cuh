@@ -93,7 +93,7 @@ struct TileArgs {
     int iters;
     int smem_stride;          // floats per line row in shared memory
     int max_re;               // boundary-map slots per line (0: no maps)
-    int vec4;                 // rows 16-byte aligned (x pass)
+    int vec4;                 // 16-byte aligned rows (x pass) or grid rows (y pass)
     int nbuf;                 // data buffers: 1 or 2 (copies overlap filtering)
 };
 
@@ -430,7 +430,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     const int yr = threadIdx.x % R, yk0 = threadIdx.x / R;
     const int64_t row_step = 32 * a.pt_stride;
     const bool maps = mre > 0;
-    const bool vec = W == 1 && a.vec4;
+    const bool vec = W == 1 && a.vec4 && a.pt_stride == 1;
 
     // Slice groups of this CTA, double buffered: the copies of the next
     // group are in flight while the current one is filtered.
@@ -446,7 +446,13 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     // rows in slice pairs with one buffer: 16-byte loads from both slices of
     // a pair, interleaved in registers into two 16-byte shared stores (the
     // copy engine cannot interleave); otherwise element-wise cp.async
-    const bool pv = W == 2 && a.vec4 && a.nbuf == 1;
+    const bool pv = W == 2 && a.vec4 && a.nbuf == 1 && a.pt_stride == 1;
+    // columns in slice pairs: each thread stores 4 adjacent columns of one
+    // row of both slices of a pair as two 16-byte stores (4 paired 8-byte
+    // shared loads), instead of 8 scalar stores
+    const bool svy = W == 2 && a.vec4 && a.pt_stride != 1 && R % 4 == 0;
+    constexpr int QY = R >= 4 ? R / 4 : 1;   // column quads per row
+    const int cq = threadIdx.x % QY, yk1 = threadIdx.x / QY, ykstep = blockDim.x / QY;
     auto issue_loads = [&](int64_t gi, int buf) {
         const int nb = group_size(gi);
         if (pv) {
@@ -592,7 +598,30 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
                 }
             }
         }
-        for (int b = 0; b < (pv ? 0 : nb); ++b) {
+        if (svy && 4 * cq < lines_here) {
+            for (int u = 0; u < (nb + 1) / 2; ++u) {
+                float *d0 = a.out + slice_of(gi, 2 * u) * a.plane + line0 + 4 * cq;
+                float *d1 = 2 * u + 1 < nb ? a.out + slice_of(gi, 2 * u + 1) * a.plane + line0 + 4 * cq
+                                           : nullptr;
+                const T *db = dt + ((int64_t)buf * U * R + (int64_t)u * R + 4 * cq) * ss;
+#pragma unroll 4
+                for (int k = yk1; k < n; k += ykstep) {
+                    float y0[4], y1[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const T v = db[i * ss + k];
+                        y0[i] = L::get(v, 0);
+                        y1[i] = L::get(v, 1);
+                    }
+                    *reinterpret_cast<float4 *>(d0 + (int64_t)k * a.pt_stride) =
+                        make_float4(y0[0], y0[1], y0[2], y0[3]);
+                    if (d1)
+                        *reinterpret_cast<float4 *>(d1 + (int64_t)k * a.pt_stride) =
+                            make_float4(y1[0], y1[1], y1[2], y1[3]);
+                }
+            }
+        }
+        for (int b = 0; b < (pv || svy ? 0 : nb); ++b) {
             float *dst = a.out + slice_of(gi, b) * a.plane;
             const float *db = ds + (int64_t)buf * B * R * ss + (b / W) * W * R * ss + b % W;
             if (a.pt_stride == 1) {
