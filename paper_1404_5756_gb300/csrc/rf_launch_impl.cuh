@@ -75,7 +75,7 @@ void launch_multi_rb(const MultiArgs &m, unsigned grid, size_t smem, cudaStream_
 // of the planner).
 #define RF_FOR_EACH_SHAPE(X)                                                   \
     X(8, 4) X(8, 2) X(8, 1) X(4, 4) X(4, 2) X(4, 1) X(2, 4) X(2, 1) X(1, 4)    \
-    X(1, 1) X(1, 8) X(2, 8) X(4, 8) X(8, 8)
+    X(1, 1) X(1, 8) X(2, 8) X(4, 8) X(8, 8) X(16, 4) X(16, 8)
 
 template <int ORDER, bool ADJ>
 void launch_shape(const TileArgs &a, TileShape sh, int64_t nlines, int64_t groups,

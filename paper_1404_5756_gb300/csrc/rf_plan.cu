@@ -405,9 +405,11 @@ void choose_chunk(Dir &q)
 // (lines per CTA, slices per thread) pairs the tile kernel is built for
 // (rf_launch_impl.cuh), in order of preference.
 constexpr TileShape kShapesY[] = {{8, 4}, {8, 2}, {4, 4}, {8, 1}, {4, 2}, {2, 4},
-                                  {4, 1}, {2, 1}, {1, 4}, {1, 1}, {1, 8}, {2, 8}, {4, 8}, {8, 8}};
+                                  {4, 1}, {2, 1}, {1, 4}, {1, 1}, {1, 8}, {2, 8}, {4, 8}, {8, 8},
+                                  {16, 4}, {16, 8}};
 constexpr TileShape kShapesX[] = {{4, 4}, {8, 4}, {2, 4}, {4, 2}, {8, 2}, {4, 1},
-                                  {8, 1}, {1, 4}, {2, 1}, {1, 1}, {1, 8}, {2, 8}, {4, 8}, {8, 8}};
+                                  {8, 1}, {1, 4}, {2, 1}, {1, 1}, {1, 8}, {2, 8}, {4, 8}, {8, 8},
+                                  {16, 4}, {16, 8}};
 
 rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
                     const float *L_dev, const std::vector<int32_t> &base,
