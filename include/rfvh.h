@@ -219,6 +219,13 @@ rf_status rf_graph_launch(rf_graph g, void *stream);
  * accepted. */
 rf_status rf_graph_destroy(rf_graph g);
 
+/* Text description of the plan (domains, chunking, the launch
+ * configurations chosen so far per variable count, level batch and
+ * direction, multi-domain shapes) into buf, at most cap - 1 characters plus
+ * a terminating NUL (truncated if longer).  Errors: RF_EINVAL (null plan or
+ * buffer, cap == 0). */
+rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap);
+
 /* Sticky status of the plan: RF_OK, or the first error a launch or a
  * device-side check recorded since the plan was built. */
 rf_status rf_plan_status(rf_plan p);

@@ -77,6 +77,7 @@ def load(build_if_missing: bool = False):
     lib.rf_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i),
                                  ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.rf_plan_destroy.argtypes = [vp]
+    lib.rf_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.rf_graph_create.argtypes = [vp, pp, pp, i, i, ctypes.POINTER(vp)]
     lib.rf_graph_launch.argtypes = [vp, vp]
     lib.rf_graph_destroy.argtypes = [vp]
@@ -85,7 +86,7 @@ def load(build_if_missing: bool = False):
     for name in ("rf_options_default", "rf_coeffs", "rf_apply", "rf_apply_adjoint",
                  "rf_apply_host", "rf_apply_static", "rf_plan_tune", "rf_plan_tune_batch",
                  "rf_plan_status",
-                 "rf_plan_info", "rf_plan_destroy", "rf_graph_create", "rf_graph_launch",
+                 "rf_plan_info", "rf_plan_destroy", "rf_plan_describe", "rf_graph_create", "rf_graph_launch",
                  "rf_graph_destroy"):
         getattr(lib, name).restype = i
     _lib = lib
@@ -165,6 +166,12 @@ def rf_plan_info(plan):
     check(load().rf_plan_info(plan, ctypes.byref(pts), ctypes.byref(nd),
                               ctypes.byref(nb), ctypes.byref(nl)), "rf_plan_info")
     return pts.value, nd.value, nb.value, nl.value
+
+
+def rf_plan_describe(plan) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(load().rf_plan_describe(plan, buf, len(buf)), "rf_plan_describe")
+    return buf.value.decode()
 
 
 def rf_plan_destroy(plan) -> None:

@@ -7,7 +7,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <new>
 #include <mutex>
 #include <vector>
@@ -1477,6 +1479,59 @@ rf_status rf_plan_tune(rf_plan p, int nvar, void *stream)
 {
     if (!p || nvar < 1) return RF_EINVAL;
     return tune_impl(p, nvar, (cudaStream_t)stream);
+}
+
+rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
+{
+    if (!p || !buf || cap == 0) return RF_EINVAL;
+    std::string t;
+    char line[256];
+    for (size_t d = 0; d < p->dom.size(); ++d) {
+        const Domain &D = p->dom[d];
+        std::snprintf(line, sizeof line, "domain %zu: %lld x %lld x %lld, coefficient levels %lld\n", d,
+                      (long long)D.g.nx, (long long)D.g.ny, (long long)D.g.nz, (long long)D.ncl);
+        t += line;
+        for (const auto &e : D.batch) {
+            std::snprintf(line, sizeof line, "  nvar %lld: %lld levels per batch\n",
+                          (long long)e.first, (long long)e.second);
+            t += line;
+        }
+        for (int dir = 0; dir < 2; ++dir) {
+            const Dir &q = D.d[dir];
+            std::snprintf(line, sizeof line, "  %s: lines %lld of %lld points, chunk %lld, segment ends %lld\n",
+                          dir == 0 ? "x" : "y", (long long)q.nlines, (long long)q.n, (long long)q.C,
+                          (long long)q.ntail);
+            t += line;
+            for (const CfgEntry &e : q.cfgs) {
+                if (e.cfg.tile)
+                    std::snprintf(line, sizeof line,
+                                  "    nvar %lld, %lld levels, %s: tile R=%d B=%d buffers=%d smem=%zu "
+                                  "CTAs/SM=%d rows=%lld\n",
+                                  (long long)e.nvar, (long long)e.nk, e.adjoint ? "adjoint" : "forward",
+                                  e.cfg.sh.R, e.cfg.sh.B, e.cfg.nbuf, e.cfg.smem, e.cfg.occ,
+                                  (long long)e.cfg.groups);
+                else
+                    std::snprintf(line, sizeof line, "    nvar %lld, %lld levels, %s: line kernel\n",
+                                  (long long)e.nvar, (long long)e.nk, e.adjoint ? "adjoint" : "forward");
+                t += line;
+            }
+        }
+    }
+    for (const MultiCfg &c : p->mcfg) {
+        std::snprintf(line, sizeof line, "multi-domain %s %s, nvar %lld: R=%d B=%d smem=%zu CTAs/SM=%d\n",
+                      c.dir == 0 ? "x" : "y", c.adjoint ? "adjoint" : "forward", (long long)c.nvar,
+                      c.sh.R, c.sh.B, c.smem, c.occ);
+        t += line;
+    }
+    for (const auto &e : p->multi_pref) {
+        std::snprintf(line, sizeof line, "nvar %lld: %s launches\n", (long long)e.first,
+                      e.second ? "multi-domain" : "per-domain");
+        t += line;
+    }
+    const size_t n = std::min(cap - 1, t.size());
+    std::memcpy(buf, t.data(), n);
+    buf[n] = '\0';
+    return RF_OK;
 }
 
 rf_status rf_plan_status(rf_plan p)

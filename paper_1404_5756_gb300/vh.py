@@ -105,6 +105,10 @@ class Plan:
         with torch.cuda.device(self.device):
             _lib.rf_plan_tune_batch(self._plan, nvar, _stream_handle(self.device))
 
+    def describe(self) -> str:
+        """The plan's chunking and the launch configurations chosen so far."""
+        return _lib.rf_plan_describe(self._plan)
+
     def status(self) -> int:
         return _lib.rf_plan_status(self._plan)
 

@@ -290,6 +290,8 @@ def test_tuned_shapes_give_identical_results():
         assert torch.equal(plan.apply(x), ref_f)
         assert torch.equal(plan.apply_adjoint(x), ref_a)
         assert plan.status() == 0
+        text = plan.describe()
+        assert "x: lines 384 of 1024 points" in text and "tile R=" in text
 
 
 @pytest.mark.parametrize("order,K", FILTERS)
