@@ -1,7 +1,7 @@
 // rf_launch_impl.cuh -- host-side launch code of the tile kernels (one
 // domain and many domains).  Included by the translation units that
-// instantiate it for one filter order and direction each (rf_tiles_*.cu), so
-// the kernels compile in parallel.
+// instantiate it for one filter order, direction and lanes-per-line value
+// each (rf_tiles_*.cu), so the kernels compile in parallel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -16,7 +16,7 @@ namespace {
 // Raise a kernel's dynamic shared-memory limit once per device and size, so
 // a launch inside a stream capture makes no attribute call.
 constexpr int kAttrDevices = 64;
-template <int ORDER, bool ADJ, int R, int B, bool MULTI>
+template <int ORDER, bool ADJ, int R, int B, int P, bool MULTI>
 void smem_attr(size_t smem)
 {
     static std::mutex mu;
@@ -26,35 +26,35 @@ void smem_attr(size_t smem)
     std::lock_guard<std::mutex> lock(mu);
     if (dev >= 0 && dev < kAttrDevices && smem <= done[dev]) return;
     if (MULTI)
-        cudaFuncSetAttribute(tile_multi_kernel<ORDER, ADJ, R, B>,
+        cudaFuncSetAttribute(tile_multi_kernel<ORDER, ADJ, R, B, P>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else
-        cudaFuncSetAttribute(tile_kernel<ORDER, ADJ, R, B>,
+        cudaFuncSetAttribute(tile_kernel<ORDER, ADJ, R, B, P>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < kAttrDevices) done[dev] = smem;
 }
 
-template <int ORDER, bool ADJ, int R, int B>
+template <int ORDER, bool ADJ, int R, int B, int P>
 void launch_tile(const TileArgs &a, int64_t nlines, int64_t groups, size_t smem,
                  cudaStream_t st)
 {
-    smem_attr<ORDER, ADJ, R, B, false>(smem);
+    smem_attr<ORDER, ADJ, R, B, P, false>(smem);
     dim3 grid((unsigned)((nlines + R - 1) / R), (unsigned)groups);
-    tile_kernel<ORDER, ADJ, R, B><<<grid, 32 * R, smem, st>>>(a);
+    tile_kernel<ORDER, ADJ, R, B, P><<<grid, R * P, smem, st>>>(a);
 }
 
-template <int ORDER, bool ADJ, int R, int B, bool MULTI>
+template <int ORDER, bool ADJ, int R, int B, int P, bool MULTI>
 int tile_occupancy(size_t smem)
 {
-    smem_attr<ORDER, ADJ, R, B, MULTI>(smem);
+    smem_attr<ORDER, ADJ, R, B, P, MULTI>(smem);
     int blocks = 0;
     cudaError_t e;
     if (MULTI)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &blocks, tile_multi_kernel<ORDER, ADJ, R, B>, 32 * R, smem);
+            &blocks, tile_multi_kernel<ORDER, ADJ, R, B, P>, R * P, smem);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_kernel<ORDER, ADJ, R, B>,
-                                                          32 * R, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_kernel<ORDER, ADJ, R, B, P>,
+                                                          R * P, smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -62,64 +62,70 @@ int tile_occupancy(size_t smem)
     return blocks;
 }
 
-template <int ORDER, bool ADJ, int R, int B>
+template <int ORDER, bool ADJ, int R, int B, int P>
 void launch_multi_rb(const MultiArgs &m, unsigned grid, size_t smem, cudaStream_t st)
 {
-    smem_attr<ORDER, ADJ, R, B, true>(smem);
-    tile_multi_kernel<ORDER, ADJ, R, B><<<grid, 32 * R, smem, st>>>(m);
+    smem_attr<ORDER, ADJ, R, B, P, true>(smem);
+    tile_multi_kernel<ORDER, ADJ, R, B, P><<<grid, R * P, smem, st>>>(m);
 }
 
 }  // namespace
 
 // The shapes the tile kernel is built for (kept in step with the shape lists
-// of the planner).
-#define RF_FOR_EACH_SHAPE(X)                                                   \
-    X(8, 4) X(8, 2) X(8, 1) X(4, 4) X(4, 2) X(4, 1) X(2, 4) X(2, 1) X(1, 4)    \
-    X(1, 1) X(1, 8) X(2, 8) X(4, 8) X(8, 8) X(16, 4) X(16, 8)
+// of the planner); each translation unit builds the shapes of one lanes-per-
+// line value.
+#define RF_FOR_EACH_SHAPE(X)                                                          \
+    X(8, 4, 32) X(8, 2, 32) X(8, 1, 32) X(4, 4, 32) X(2, 4, 32) X(1, 4, 32) X(1, 1, 32) \
+    X(1, 8, 32) X(2, 8, 32) X(4, 8, 32) X(8, 8, 32) X(16, 4, 32) X(16, 8, 32)          \
+    X(4, 4, 16) X(8, 4, 16) X(16, 4, 16) X(8, 8, 16) X(16, 8, 16) X(8, 2, 16)          \
+    X(16, 2, 16) X(8, 1, 16)
 
-template <int ORDER, bool ADJ>
-void launch_shape(const TileArgs &a, TileShape sh, int64_t nlines, int64_t groups,
-                  size_t smem, cudaStream_t st)
+template <int ORDER, bool ADJ, int P>
+void launch_shape_p(const TileArgs &a, TileShape sh, int64_t nlines, int64_t groups,
+                    size_t smem, cudaStream_t st)
 {
-#define RF_SHAPE(r, b)                                                           \
-    if (sh.R == r && sh.B == b) {                                                \
-        launch_tile<ORDER, ADJ, r, b>(a, nlines, groups, smem, st);              \
-        return;                                                                  \
-    }
+#define RF_SHAPE(r, b, p)                                                        \
+    if constexpr (p == P)                                                        \
+        if (sh.R == r && sh.B == b) {                                            \
+            launch_tile<ORDER, ADJ, r, b, p>(a, nlines, groups, smem, st);       \
+            return;                                                              \
+        }
     RF_FOR_EACH_SHAPE(RF_SHAPE)
 #undef RF_SHAPE
 }
 
-template <int ORDER, bool ADJ, bool MULTI>
-int shape_occupancy(TileShape sh, size_t smem)
+template <int ORDER, bool ADJ, bool MULTI, int P>
+int shape_occupancy_p(TileShape sh, size_t smem)
 {
-#define RF_SHAPE(r, b) \
-    if (sh.R == r && sh.B == b) return tile_occupancy<ORDER, ADJ, r, b, MULTI>(smem);
+#define RF_SHAPE(r, b, p)                                                        \
+    if constexpr (p == P)                                                        \
+        if (sh.R == r && sh.B == b) return tile_occupancy<ORDER, ADJ, r, b, p, MULTI>(smem);
     RF_FOR_EACH_SHAPE(RF_SHAPE)
 #undef RF_SHAPE
     return 0;
 }
 
-template <int ORDER, bool ADJ>
-void launch_multi(const MultiArgs &m, TileShape sh, unsigned grid, size_t smem, cudaStream_t st)
+template <int ORDER, bool ADJ, int P>
+void launch_multi_p(const MultiArgs &m, TileShape sh, unsigned grid, size_t smem, cudaStream_t st)
 {
-#define RF_SHAPE(r, b)                                                   \
-    if (sh.R == r && sh.B == b) {                                        \
-        launch_multi_rb<ORDER, ADJ, r, b>(m, grid, smem, st);            \
-        return;                                                          \
-    }
+#define RF_SHAPE(r, b, p)                                                \
+    if constexpr (p == P)                                                \
+        if (sh.R == r && sh.B == b) {                                    \
+            launch_multi_rb<ORDER, ADJ, r, b, p>(m, grid, smem, st);     \
+            return;                                                      \
+        }
     RF_FOR_EACH_SHAPE(RF_SHAPE)
 #undef RF_SHAPE
 }
 
 #undef RF_FOR_EACH_SHAPE
 
-#define RF_INSTANTIATE(O, A)                                                              \
-    template void launch_shape<O, A>(const TileArgs &, TileShape, int64_t, int64_t, size_t, \
-                                     cudaStream_t);                                       \
-    template int shape_occupancy<O, A, false>(TileShape, size_t);                         \
-    template int shape_occupancy<O, A, true>(TileShape, size_t);                          \
-    template void launch_multi<O, A>(const MultiArgs &, TileShape, unsigned, size_t,       \
-                                     cudaStream_t);
+#define RF_INSTANTIATE(O, A, P)                                                             \
+    template void launch_shape_p<O, A, P>(const TileArgs &, TileShape, int64_t, int64_t,    \
+                                          size_t, cudaStream_t);                            \
+    template int shape_occupancy_p<O, A, false, P>(TileShape, size_t);                      \
+    template int shape_occupancy_p<O, A, true, P>(TileShape, size_t);                       \
+    template void launch_multi_p<O, A, P>(const MultiArgs &, TileShape, unsigned, size_t,    \
+                                          cudaStream_t);
 
 }  // namespace rfvh

@@ -55,10 +55,11 @@ struct Dir {
     float4 *coef = nullptr;          // [ncl][nlines][n]
     int32_t *tail_base = nullptr;    // [ncl*nlines + 1] first boundary map of each line
     float2 *tmap = nullptr;          // [ntail][9] hi/lo pairs, consecutive along each line
-    float *xfer = nullptr;           // [ncl][nlines][32][XF]
+    int P = 32;                      // lanes per line of the tile kernel (32 or 16)
+    float *xfer = nullptr;           // [ncl][nlines][P][XF]
     float4 *coef_il_base = nullptr;  // interleaved coefficients with guards
-    float4 *coef_il = nullptr;       // [ncl][nlines][C][32] (tile kernel)
-    LaneInfo *lanes = nullptr;       // [ncl][nlines][32]
+    float4 *coef_il = nullptr;       // [ncl][nlines][C][P] (tile kernel)
+    LaneInfo *lanes = nullptr;       // [ncl][nlines][P]
     int64_t ntail = 0;
     int max_re = 0;                  // most segment ends on one line
     std::vector<CfgEntry> cfgs;      // launch shapes chosen so far
@@ -251,18 +252,23 @@ __device__ void mm3(const double *P, const double *Q, double *O)
 }
 
 // Lane-interleaved copy of one direction's coefficients for the tile kernel
-// (step j of lane l of a line at [line][j][l], points past the line's end
-// are land), with the segment-end flags moved into per-lane bit masks and
-// the rank of each lane's first segment end on its line.  One warp per line.
-__global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C,
+// (step j of lane l of a line at [line][j][l], P lanes per line, points past
+// the line's end are land), with the segment-end flags moved into per-lane
+// bit masks and the rank of each lane's first segment end on its line.  P
+// threads per line; a warp's lines past the end work on the last line (every
+// lane joins the shuffles) and write nothing.
+__global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C, int P,
                                   const float4 *__restrict__ coef, float4 *__restrict__ il,
                                   LaneInfo *__restrict__ lanes)
 {
-    const int64_t line = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
-    const int lane = threadIdx.x & 31;
-    if (line >= nlines_total) return;   // whole warps exit together
+    const int64_t line0 = blockIdx.x * (int64_t)(blockDim.x / P) + threadIdx.x / P;
+    const int lane = threadIdx.x % P;
+    if (blockIdx.x * (int64_t)(blockDim.x / P) + (threadIdx.x / 32) * (32 / P) >= nlines_total)
+        return;   // whole warps past the end exit together
+    const bool ok = line0 < nlines_total;
+    const int64_t line = ok ? line0 : nlines_total - 1;
     const float4 *src = coef + line * n;
-    float4 *dst = il + line * C * 32 + lane;
+    float4 *dst = il + line * C * P + lane;
     unsigned long long bits[2] = {0ull, 0ull};
     for (int j = 0; j < C; ++j) {
         const int64_t k = (int64_t)lane * C + j;
@@ -271,12 +277,12 @@ __global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C,
             bits[j >> 6] |= 1ull << (j & 63);
             c.x = fabsf(c.x);
         }
-        dst[(int64_t)j * 32] = c;
+        if (ok) dst[(int64_t)j * P] = c;
     }
     const int nre = __popcll(bits[0]) + __popcll(bits[1]);
     int incl = nre;
-    for (int d = 1; d < 32; d <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    for (int d = 1; d < P; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, d, P);
         if (lane >= d) incl += t;
     }
     LaneInfo li;
@@ -284,7 +290,7 @@ __global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C,
     li.re.hi = bits[1];
     li.rank0 = incl - nre;
     li.nre = nre;
-    lanes[line * 32 + lane] = li;
+    if (ok) lanes[line * P + lane] = li;
 }
 
 // Chunk transfer matrices (zero-input maps across one lane's chunk), FP64
@@ -292,12 +298,12 @@ __global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C,
 // A_a..A_{b-1} (zero if the chunk holds a segment end), adjoint causal
 // (A_a..A_{b-1})^T, adjoint anticausal (A_{b-1}..A_a)^T (zero if a segment
 // end).  Empty chunks get identities.
-__global__ void xfer_kernel(int64_t nrec, int64_t n, int64_t C, int order,
+__global__ void xfer_kernel(int64_t nrec, int64_t n, int64_t C, int P, int order,
                             const float4 *__restrict__ coef, float *__restrict__ xfer)
 {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= nrec) return;
-    const int64_t line = idx / 32, lane = idx - line * 32;
+    const int64_t line = idx / P, lane = idx - line * P;
     const int64_t a = lane * C, b = min(a + C, n);
     const float4 *cf = coef + line * n;
     const int M = order == 3 ? 9 : 1;
@@ -394,24 +400,35 @@ int64_t smem_stride(int64_t n)
     return n + ((4 - n % 32) + 32) % 32;   // row stride = 4 (mod 32) floats
 }
 
-// Chunk length of the tile kernel for line length n (odd, so the lanes'
-// shared-memory accesses fall in distinct banks), or 0 when the line is
-// too long for it.
-void choose_chunk(Dir &q)
+// Lanes per line and chunk length of the tile kernel for line length n.
+// Third-order lines of up to 1008 points take 16 lanes (two lines per warp):
+// chunks of up to 63 points instead of half that, and a scan over 16 lanes
+// (one step fewer, over twice the points), which pays where the 3x3 scans
+// are dear.  The first-order filter keeps 32 lanes: its scans are cheap and
+// its short recursion prefers more, shorter chunks.  C is odd, so the lanes'
+// shared-memory accesses fall in distinct banks.  R = 0 marks lines too long
+// for the tile kernel.
+void choose_chunk(Dir &q, int order)
 {
-    q.C = (q.n + 31) / 32;
+    q.P = order == 3 && q.n <= 1008 ? 16 : 32;
+    q.C = (q.n + q.P - 1) / q.P;
     if (q.C % 2 == 0) ++q.C;
     q.R = q.C <= kMaxChunk ? 1 : 0;   // R > 0 marks "tile kernel usable"
 }
 
-// (lines per CTA, slices per thread) pairs the tile kernel is built for
-// (rf_launch_impl.cuh), in order of preference.
-constexpr TileShape kShapesY[] = {{8, 4}, {8, 2}, {4, 4}, {8, 1}, {4, 2}, {2, 4},
-                                  {4, 1}, {2, 1}, {1, 4}, {1, 1}, {1, 8}, {2, 8}, {4, 8}, {8, 8},
-                                  {16, 4}, {16, 8}};
-constexpr TileShape kShapesX[] = {{4, 4}, {8, 4}, {2, 4}, {4, 2}, {8, 2}, {4, 1},
-                                  {8, 1}, {1, 4}, {2, 1}, {1, 1}, {1, 8}, {2, 8}, {4, 8}, {8, 8},
-                                  {16, 4}, {16, 8}};
+// (lines per CTA, slices per thread, lanes per line) shapes the tile kernel
+// is built for (rf_launch_impl.cuh), in order of preference; a direction
+// uses the shapes with its own lanes per line.
+constexpr TileShape kShapesY[] = {
+    {8, 4, 32},  {8, 2, 32},  {4, 4, 32},  {8, 1, 32},  {2, 4, 32},  {1, 4, 32},
+    {1, 1, 32},  {1, 8, 32},  {2, 8, 32},  {4, 8, 32},  {8, 8, 32},  {16, 4, 32},
+    {16, 8, 32}, {16, 4, 16}, {8, 4, 16},  {16, 8, 16}, {8, 8, 16},  {4, 4, 16},
+    {16, 2, 16}, {8, 2, 16},  {8, 1, 16}};
+constexpr TileShape kShapesX[] = {
+    {4, 4, 32},  {8, 4, 32},  {2, 4, 32},  {8, 2, 32},  {8, 1, 32},  {1, 4, 32},
+    {1, 1, 32},  {1, 8, 32},  {2, 8, 32},  {4, 8, 32},  {8, 8, 32},  {16, 4, 32},
+    {16, 8, 32}, {4, 4, 16},  {8, 4, 16},  {16, 4, 16}, {8, 8, 16},  {16, 8, 16},
+    {8, 2, 16},  {16, 2, 16}, {8, 1, 16}};
 
 rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
                     const float *L_dev, const std::vector<int32_t> &base,
@@ -425,7 +442,7 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
     q.line_stride = dir == 0 ? g.nx : 1;
     q.ntail = (int64_t)sp.size();
     q.max_re = max_re;
-    choose_chunk(q);
+    choose_chunk(q, P->opt.order);
     const int64_t plane = g.nx * g.ny, ncl = D.ncl;
     const int o = P->opt.order, K = P->opt.iters, nm = P->opt.norm;
     const int qc = (P->opt.flags & RF_FLAG_Q_CORRECTED) ? 1 : 0;
@@ -435,12 +452,12 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
     RF_TRY(dev_alloc(&q.tail_base, (int64_t)base.size(), &P->bytes));
     RF_TRY(dev_alloc(&q.tmap, 9 * q.ntail, &P->bytes));
     if (q.R > 0) {
-        RF_TRY(dev_alloc(&q.xfer, ncl * q.nlines * 32 * XS, &P->bytes));
-        RF_TRY(dev_alloc(&q.coef_il_base, ncl * q.nlines * q.C * 32 + 2 * kCoefGuard, &P->bytes));
-        RF_TRY(dev_alloc(&q.lanes, ncl * q.nlines * 32, &P->bytes));
+        RF_TRY(dev_alloc(&q.xfer, ncl * q.nlines * q.P * XS, &P->bytes));
+        RF_TRY(dev_alloc(&q.coef_il_base, ncl * q.nlines * q.C * q.P + 2 * kCoefGuard, &P->bytes));
+        RF_TRY(dev_alloc(&q.lanes, ncl * q.nlines * q.P, &P->bytes));
         q.coef_il = q.coef_il_base + kCoefGuard;
         RF_TRY(cuda_status(cudaMemsetAsync(q.coef_il_base, 0,
-                                           sizeof(float4) * (size_t)(ncl * q.nlines * q.C * 32 +
+                                           sizeof(float4) * (size_t)(ncl * q.nlines * q.C * q.P +
                                                                      2 * kCoefGuard), st)));
     }
     RF_TRY(cuda_status(cudaMemcpyAsync(q.tail_base, base.data(), base.size() * 4,
@@ -450,13 +467,13 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
         ncl, g.nx, g.ny, dir, mask_dev, g.mask_nz, L_dev, g.L_nz, o, K, nm, qc, q.coef);
     RF_TRY(cuda_status(cudaGetLastError()));
     if (q.R > 0) {
-        const int64_t nrec = ncl * q.nlines * 32;
-        xfer_kernel<<<(unsigned)((nrec + 127) / 128), 128, 0, st>>>(nrec, q.n, q.C, o,
+        const int64_t nrec = ncl * q.nlines * q.P;
+        xfer_kernel<<<(unsigned)((nrec + 127) / 128), 128, 0, st>>>(nrec, q.n, q.C, q.P, o,
                                                                       q.coef, q.xfer);
         RF_TRY(cuda_status(cudaGetLastError()));
-        const int64_t nl = ncl * q.nlines;
-        interleave_kernel<<<(unsigned)((nl + 3) / 4), 128, 0, st>>>(nl, q.n, (int)q.C, q.coef,
-                                                                     q.coef_il, q.lanes);
+        const int64_t nl = ncl * q.nlines, lpb = 128 / q.P;
+        interleave_kernel<<<(unsigned)((nl + lpb - 1) / lpb), 128, 0, st>>>(
+            nl, q.n, (int)q.C, q.P, q.coef, q.coef_il, q.lanes);
         RF_TRY(cuda_status(cudaGetLastError()));
     }
     if (!sp.empty()) {
@@ -538,7 +555,7 @@ bool finish_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk, LaunchC
 {
     const int64_t nslices = nvar * nk;
     const int64_t per_cta = D.ncl > 1 ? nvar : nslices;
-    if (q.R == 0 || (L.sh.B > 1 && L.sh.B > per_cta)) return false;
+    if (q.R == 0 || L.sh.P != q.P || (L.sh.B > 1 && L.sh.B > per_cta)) return false;
     L.smem = (size_t)tile_smem_bytes(L.sh.R, L.sh.B, smem_stride(q.n), q.max_re, L.nbuf);
     if (L.smem > kSmemMax) return false;
     L.occ = shape_occupancy<ORDER, ADJ, false>(L.sh, L.smem);
@@ -761,7 +778,7 @@ bool multi_fits(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, size_t *
     bool any = false;
     for (const Domain &D : p->dom) {
         const Dir &q = D.d[dir];
-        if (q.R == 0) continue;
+        if (q.R == 0 || q.P != sh.P) continue;   // launched on their own
         m = std::max(m, (size_t)tile_smem_bytes(sh.R, sh.B, smem_stride(q.n), q.max_re, 1));
         any = true;
     }
@@ -803,7 +820,7 @@ MultiCfg multi_cfg(rf_plan_ *p, int dir, int64_t nvar, bool adjoint)
         for (const TileShape &sh : dir == 1 ? kShapesY : kShapesX) {
             MultiCfg t;
             if (multi_try_any(p, dir, nvar, adjoint, sh, t) &&
-                (pass == 1 || (t.smem <= kSmemTarget && t.occ * sh.R >= 8))) {
+                (pass == 1 || (t.smem <= kSmemTarget && t.occ * sh.R * sh.P / 32 >= 8))) {
                 c = t;
                 found = true;
                 break;
@@ -820,7 +837,7 @@ rf_status multi_pass(rf_plan_ *p, const MultiCfg &c, const float *const *src,
 {
     std::vector<int> doms;
     for (size_t d = 0; d < p->dom.size(); ++d)
-        if (p->dom[d].d[c.dir].R > 0) doms.push_back((int)d);
+        if (p->dom[d].d[c.dir].R > 0 && p->dom[d].d[c.dir].P == c.sh.P) doms.push_back((int)d);
     const int iters = p->opt.order == 3 ? 1 : p->opt.iters;
     for (size_t c0 = 0; c0 < doms.size(); c0 += kMaxMulti) {
         MultiArgs m{};
@@ -864,24 +881,35 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
                       bool adjoint, bool dry, cudaStream_t st)
 {
     if (!p->queue) RF_TRY(dev_alloc(&p->queue, 1, &p->bytes));
+    MultiCfg cs[2];
+    for (int dir = 0; dir < 2; ++dir) cs[dir] = multi_cfg(p, dir, nvar, adjoint);
+    // domains a pass's multi-domain launch does not cover (lines too long
+    // for the tile kernel, or other lanes per line) launch on their own
+    auto covered = [&](const Dir &q, const MultiCfg &c) {
+        return c.occ > 0 && q.R > 0 && q.P == c.sh.P;
+    };
     for (Domain &D : p->dom) {
         int64_t nt = 0;
-        for (int dir = 0; dir < 2; ++dir)
-            if (D.d[dir].R == 0) nt = std::max(nt, D.d[dir].ntail);
+        for (int dir = 0; dir < 2; ++dir) {
+            const Dir &q = D.d[dir];
+            if (covered(q, cs[dir])) continue;
+            if (q.R == 0 || !cfg_of(p, D, dir, nvar, D.g.nz, adjoint).tile)
+                nt = std::max(nt, q.ntail);
+        }
         RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * D.g.nz * nt * 3, &p->bytes));
     }
+    if (dry) return RF_OK;
     const int K = p->opt.iters;
     for (int pass = 0; pass < 2; ++pass) {
         const int dir = adjoint ? 1 - pass : pass;
-        const MultiCfg c = multi_cfg(p, dir, nvar, adjoint);
-        if (dry) continue;
+        const MultiCfg &c = cs[dir];
         const float *const *src = pass == 0 ? in : (const float *const *)out;
         if (c.occ > 0) RF_TRY(multi_pass(p, c, src, out, nvar, adjoint, st));
         for (size_t d = 0; d < p->dom.size(); ++d) {
             Domain &D = p->dom[d];
             const Dir &q = D.d[dir];
-            if (q.R > 0) continue;
-            const LaunchCfg L{};   // long-line kernel
+            if (covered(q, c)) continue;
+            const LaunchCfg L = q.R > 0 ? cfg_of(p, D, dir, nvar, D.g.nz, adjoint) : LaunchCfg{};
             if (p->opt.order == 3) {
                 if (adjoint) launch_dir<3, true>(D, q, L, src[d], out[d], nvar, 0, D.g.nz, 1, st);
                 else launch_dir<3, false>(D, q, L, src[d], out[d], nvar, 0, D.g.nz, 1, st);
@@ -1498,17 +1526,18 @@ rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
         }
         for (int dir = 0; dir < 2; ++dir) {
             const Dir &q = D.d[dir];
-            std::snprintf(line, sizeof line, "  %s: lines %lld of %lld points, chunk %lld, segment ends %lld\n",
-                          dir == 0 ? "x" : "y", (long long)q.nlines, (long long)q.n, (long long)q.C,
+            std::snprintf(line, sizeof line,
+                          "  %s: lines %lld of %lld points, %d lanes per line, chunk %lld, segment ends %lld\n",
+                          dir == 0 ? "x" : "y", (long long)q.nlines, (long long)q.n, q.P, (long long)q.C,
                           (long long)q.ntail);
             t += line;
             for (const CfgEntry &e : q.cfgs) {
                 if (e.cfg.tile)
                     std::snprintf(line, sizeof line,
-                                  "    nvar %lld, %lld levels, %s: tile R=%d B=%d buffers=%d smem=%zu "
+                                  "    nvar %lld, %lld levels, %s: tile R=%d B=%d P=%d buffers=%d smem=%zu "
                                   "CTAs/SM=%d rows=%lld\n",
                                   (long long)e.nvar, (long long)e.nk, e.adjoint ? "adjoint" : "forward",
-                                  e.cfg.sh.R, e.cfg.sh.B, e.cfg.nbuf, e.cfg.smem, e.cfg.occ,
+                                  e.cfg.sh.R, e.cfg.sh.B, e.cfg.sh.P, e.cfg.nbuf, e.cfg.smem, e.cfg.occ,
                                   (long long)e.cfg.groups);
                 else
                     std::snprintf(line, sizeof line, "    nvar %lld, %lld levels, %s: line kernel\n",
@@ -1518,9 +1547,9 @@ rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
         }
     }
     for (const MultiCfg &c : p->mcfg) {
-        std::snprintf(line, sizeof line, "multi-domain %s %s, nvar %lld: R=%d B=%d smem=%zu CTAs/SM=%d\n",
+        std::snprintf(line, sizeof line, "multi-domain %s %s, nvar %lld: R=%d B=%d P=%d smem=%zu CTAs/SM=%d\n",
                       c.dir == 0 ? "x" : "y", c.adjoint ? "adjoint" : "forward", (long long)c.nvar,
-                      c.sh.R, c.sh.B, c.smem, c.occ);
+                      c.sh.R, c.sh.B, c.sh.P, c.smem, c.occ);
         t += line;
     }
     for (const auto &e : p->multi_pref) {

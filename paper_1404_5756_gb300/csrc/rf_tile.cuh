@@ -1,11 +1,12 @@
-// rf_tile.cuh -- the main filter kernel: R whole lines per CTA, one warp per
-// line, the 32 lanes of a warp owning consecutive chunks of C points (C odd,
-// 32*C >= n, C <= 128).  Each thread filters B slices of its chunk at once (B
+// rf_tile.cuh -- the main filter kernel: R whole lines per CTA, P lanes per
+// line (P = 32: one line per warp; P = 16: two lines per warp, for short
+// lines), the P lanes of a line owning consecutive chunks of C points (C odd,
+// P*C >= n, C <= 128).  Each thread filters B slices of its chunk at once (B
 // independent recursions: instruction-level parallelism, and one coefficient
 // read serves B slices).  The line data of the B slices and the coastal
 // boundary maps of the CTA's lines sit in shared memory; the per-point
 // coefficients are read from global memory in a lane-interleaved layout
-// (step j of all 32 lanes is one contiguous 512-byte row, so every read is
+// (step j of all P lanes of a line is one contiguous row, so every read is
 // coalesced and stays in L1 across the four sweeps).  The chunk carries are
 // resolved with a Kogge-Stone scan of affine maps over the lanes (warp
 // shuffles).  One kernel serves both directions:
@@ -76,9 +77,9 @@ struct LaneInfo {
 struct TileArgs {
     const float *in;          // field [nslices][...] of this domain
     float *out;
-    const float4 *coef;       // [ncl][nlines][C][32] interleaved (beta, -e, -c1, -c2)
-    const LaneInfo *lanes;    // [ncl][nlines][32]
-    const float *xfer;        // [ncl][nlines][32][XF] chunk transfers
+    const float4 *coef;       // [ncl][nlines][C][P] interleaved (beta, -e, -c1, -c2)
+    const LaneInfo *lanes;    // [ncl][nlines][P]
+    const float *xfer;        // [ncl][nlines][P][XF] chunk transfers
     const int32_t *tail_base; // [ncl*nlines + 1] index of each line's first boundary map
     const float2 *tmap;       // [ntail][9] hi/lo pairs, consecutive along each line
     int64_t n, nlines;        // line length, lines per slice
@@ -161,41 +162,42 @@ __device__ __forceinline__ void mat_mat(const float *P, const float *Q, float *o
     }
 }
 
-// Exclusive scan of affine maps over the warp, for B slices sharing the maps'
-// linear parts.  Lane l holds x -> P x + v[b].  Forward (REV = false): lane l
-// receives the state entering its chunk from lanes 0..l-1; REV: from lanes
-// 31..l+1.
-template <int ORDER, bool REV, int B>
-__device__ __forceinline__ void warp_scan(float *P, float (*v)[3], int lane)
+// Exclusive scan of affine maps over the P lanes of a line (segments of P
+// lanes of the warp), for B slices sharing the maps' linear parts.  Lane l of
+// the line holds x -> Pm x + v[b].  Forward (REV = false): lane l receives the
+// state entering its chunk from lanes 0..l-1; REV: from lanes P-1..l+1.
+template <int ORDER, bool REV, int B, int P>
+__device__ __forceinline__ void warp_scan(float *Pm, float (*v)[3], int lane)
 {
     constexpr int M = XF<ORDER>::mat;
     constexpr int S = ORDER == 3 ? 3 : 1;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    for (int d = 1; d < P; d <<= 1) {
         float Pn[M], vn[B][S];
 #pragma unroll
         for (int k = 0; k < M; ++k)
-            Pn[k] = REV ? __shfl_down_sync(0xffffffffu, P[k], d) : __shfl_up_sync(0xffffffffu, P[k], d);
+            Pn[k] = REV ? __shfl_down_sync(0xffffffffu, Pm[k], d, P)
+                        : __shfl_up_sync(0xffffffffu, Pm[k], d, P);
 #pragma unroll
         for (int b = 0; b < B; ++b)
 #pragma unroll
             for (int k = 0; k < S; ++k)
-                vn[b][k] = REV ? __shfl_down_sync(0xffffffffu, v[b][k], d)
-                               : __shfl_up_sync(0xffffffffu, v[b][k], d);
-        const bool take = REV ? (lane + d < 32) : (lane >= d);
+                vn[b][k] = REV ? __shfl_down_sync(0xffffffffu, v[b][k], d, P)
+                               : __shfl_up_sync(0xffffffffu, v[b][k], d, P);
+        const bool take = REV ? (lane + d < P) : (lane >= d);
         if (take) {
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 float nv[S];
-                mat_vec<ORDER>(P, vn[b], nv);
+                mat_vec<ORDER>(Pm, vn[b], nv);
 #pragma unroll
                 for (int k = 0; k < S; ++k) v[b][k] += nv[k];
             }
-            if (d < 16) {   // the last level's composed map is never used
+            if (2 * d < P) {   // the last level's composed map is never used
                 float nP[M];
-                mat_mat<ORDER>(P, Pn, nP);
+                mat_mat<ORDER>(Pm, Pn, nP);
 #pragma unroll
-                for (int k = 0; k < M; ++k) P[k] = nP[k];
+                for (int k = 0; k < M; ++k) Pm[k] = nP[k];
             }
         }
     }
@@ -203,9 +205,9 @@ __device__ __forceinline__ void warp_scan(float *P, float (*v)[3], int lane)
     for (int b = 0; b < B; ++b)
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            const float t = REV ? __shfl_down_sync(0xffffffffu, v[b][k], 1)
-                                : __shfl_up_sync(0xffffffffu, v[b][k], 1);
-            v[b][k] = (REV ? lane == 31 : lane == 0) ? 0.f : t;
+            const float t = REV ? __shfl_down_sync(0xffffffffu, v[b][k], 1, P)
+                                : __shfl_up_sync(0xffffffffu, v[b][k], 1, P);
+            v[b][k] = (REV ? lane == P - 1 : lane == 0) ? 0.f : t;
         }
 }
 
@@ -240,7 +242,7 @@ struct LaneT<2> {
 };
 
 // One sweep over a lane's chunk for B slices.  cp points at the chunk's
-// first coefficient (consecutive steps 32 float4 apart), dp[u] at lane value
+// first coefficient (consecutive steps P float4 apart), dp[u] at lane value
 // u's first data element, len points.  CAUSAL walks up, else down.  IN_SEA
 // zeroes the input at land and writes the zero back (first read of the
 // data); WRITE stores the outputs in place.  rebits marks segment ends (bit
@@ -251,7 +253,7 @@ struct LaneT<2> {
 // (rank counting down from rk), or to zero without maps.  Coefficients are
 // fetched two steps ahead and data one step ahead, so memory latency
 // overlaps the arithmetic.
-template <int ORDER, bool ADJ, int B, bool CAUSAL, bool IN_SEA, bool WRITE, bool TAILS,
+template <int ORDER, bool ADJ, int B, int P, bool CAUSAL, bool IN_SEA, bool WRITE, bool TAILS,
           class MASK>
 __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
                                       typename LaneT<Pack<B>::W>::L::T *const *dp, int len,
@@ -267,14 +269,14 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
     int re_next;
     if (CAUSAL) re_next = rebits.first();
     else re_next = rebits.last();
-    float4 c = __ldg(cp + 32 * j);
-    float4 c1 = __ldg(cp + 32 * (j + dir));
+    float4 c = __ldg(cp + P * j);
+    float4 c1 = __ldg(cp + P * (j + dir));
     T x[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) x[u] = dp[u][j];
 #pragma unroll 2
     for (int t = 0; t < len; ++t, j += dir) {
-        const float4 c2 = __ldg(cp + 32 * (j + 2 * dir));
+        const float4 c2 = __ldg(cp + P * (j + 2 * dir));
         T xn[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) xn[u] = dp[u][j + dir];
@@ -331,18 +333,18 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
 }
 
 // Coastal boundary maps of one line, applied by the whole warp after the
-// causal sweep: for every segment end q of the line (lanes take q = lane,
-// lane + 32, ...) and every slice b, replace the recorded causal state X at
+// causal sweep: for every segment end q of the line (its P lanes take
+// q = lane, lane + P, ...) and every slice b, replace the recorded causal state X at
 // ys[b] + 3q by the anticausal start state M_q X (adjoint: M_q^T X).
 // Spreading the segment ends over the lanes keeps the compensated map
 // arithmetic out of the divergent per-point loop.
-template <int ORDER, bool ADJ, int B>
+template <int ORDER, bool ADJ, int B, int P>
 __device__ __forceinline__ void apply_line_tails(const float2 *ml, float *const *ys, int nre_line,
                                                  int lane)
 {
     constexpr int NS = ORDER == 3 ? 3 : 1;
     __syncwarp();
-    for (int q = lane; q < nre_line; q += 32) {
+    for (int q = lane; q < nre_line; q += P) {
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             float X[3] = {0.f, 0.f, 0.f};
@@ -355,23 +357,32 @@ __device__ __forceinline__ void apply_line_tails(const float2 *ml, float *const 
 }
 
 // The work of one CTA: line block bx (lines bx*R ..) and CTA row by of gy
-// rows along the slices (see the slice mapping below).
-template <int ORDER, bool ADJ, int R, int B>
+// rows along the slices (see the slice mapping below).  R*P threads: line rl
+// of the CTA is handled by lanes rl*P .. rl*P + P-1.
+template <int ORDER, bool ADJ, int R, int B, int P>
 __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t by, int64_t gy,
                                           unsigned char *smem_raw)
 {
     constexpr int XS = XF<ORDER>::size, M = XF<ORDER>::mat;
     constexpr int W = Pack<B>::W, U = Pack<B>::U;
+    constexpr int LPW = 32 / P;   // lines per warp
+    static_assert(P == 32 || P == 16, "lanes per line");
+    static_assert(R % LPW == 0, "whole warps per CTA");
     using L = typename LaneT<W>::L;
     using T = typename L::T;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int rl = threadIdx.x / P, lane = threadIdx.x % P;   // line of the CTA, lane on it
     const int n = (int)a.n, C = a.C, ss = a.smem_stride, mre = a.max_re;
     float2 *ms = reinterpret_cast<float2 *>(smem_raw + 16);
     float *ds = reinterpret_cast<float *>(ms + ((R * mre * 9 + 1) & ~1));
     float *ys = ds + a.nbuf * B * R * ss;   // after the data buffers
     const int64_t line0 = bx * R;
-    const int64_t myline = line0 + warp;
-    const bool active = myline < a.nlines;
+    const int64_t myline = line0 + rl;
+    // a warp works if its first line exists; its other lines past the end run
+    // on the last line's data (every lane must join the shuffles) and are
+    // never stored
+    const bool active = line0 + (int64_t)warp * LPW < a.nlines;
+    const int64_t lc = min(myline, a.nlines - 1);
     const int lines_here = (int)min((int64_t)R, a.nlines - line0);
 
     // A launch filters levels k0 .. k0+nk-1 of all nvar variables.  Slices are
@@ -398,19 +409,19 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     }
     // my chunk [ka, kb); lanes past the line's end get an empty chunk at n
     const int ka = min(lane * C, n), kb = min(ka + C, n), len = kb - ka;
-    const float4 *cg = a.coef + ((lvl_lines + min(myline, a.nlines - 1)) * C) * 32 + lane;
-    const float2 *ml = ms + warp * mre * 9;
+    const float4 *cg = a.coef + ((lvl_lines + lc) * C) * P + lane;
+    const float2 *ml = ms + rl * mre * 9;
     SegBits rebits{0ull, 0ull};
     int rank0 = 0, nre = 0, line_re = 0;
     float Pc[M], Pa[M];
     if (active) {
-        const LaneInfo li = a.lanes[(lvl_lines + myline) * 32 + lane];
+        const LaneInfo li = a.lanes[(lvl_lines + lc) * P + lane];
         rebits = li.re;
         rank0 = li.rank0;
         nre = li.nre;
         if (mre > 0)
-            line_re = (int)(a.tail_base[lvl_lines + myline + 1] - a.tail_base[lvl_lines + myline]);
-        const float *x = a.xfer + ((lvl_lines + myline) * 32 + lane) * XS;
+            line_re = (int)(a.tail_base[lvl_lines + lc + 1] - a.tail_base[lvl_lines + lc]);
+        const float *x = a.xfer + ((lvl_lines + lc) * P + lane) * XS;
         const int oc = ADJ ? 2 : 0, oa = ADJ ? 3 : 1;
 #pragma unroll
         for (int k = 0; k < M; ++k) {
@@ -424,11 +435,11 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     T *dl[U];
     float *yl[B];
 #pragma unroll
-    for (int b = 0; b < B; ++b) yl[b] = ys + (b * R + warp) * mre * 3;
+    for (int b = 0; b < B; ++b) yl[b] = ys + (b * R + rl) * mre * 3;
     // load/store mapping: the x pass copies rows, the y pass R-column
-    // strips, thread t owning column r = t % R and rows t / R + 32 m
+    // strips, thread t owning column r = t % R and rows t / R + P m
     const int yr = threadIdx.x % R, yk0 = threadIdx.x / R;
-    const int64_t row_step = 32 * a.pt_stride;
+    const int64_t row_step = (int64_t)P * a.pt_stride;
     const bool maps = mre > 0;
     const bool vec = W == 1 && a.vec4 && a.pt_stride == 1;
 
@@ -496,7 +507,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
             } else if (yr < lines_here) {
                 const float *g = src + (line0 + yr) + (int64_t)yk0 * a.pt_stride;
                 float *s = db + W * yr * ss;
-                for (int k = yk0; k < n; k += 32, g += row_step) cp_async4(s + W * k, g);
+                for (int k = yk0; k < n; k += P, g += row_step) cp_async4(s + W * k, g);
             }
         }
         asm volatile("cp.async.commit_group;\n" ::);
@@ -513,24 +524,24 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
         __syncthreads();   // group gi has landed; the other buffer is free
         if (dbl && gi + g_step < ngroups) issue_loads(gi + g_step, buf ^ 1);
 #pragma unroll
-        for (int u = 0; u < U; ++u) dl[u] = dt + ((int64_t)buf * U * R + u * R + warp) * ss + ka;
+        for (int u = 0; u < U; ++u) dl[u] = dt + ((int64_t)buf * U * R + u * R + rl) * ss + ka;
         // the filter work of the group, for the chunk's segment-end mask type
         auto filter = [&](auto rebits) {
             using MASK = decltype(rebits);
             for (int it = 0; it < a.iters; ++it) {
                 T st[U][3];
-                float v[B][3], P[M];
+                float v[B][3], Pm[M];
                 // ---- A: causal, zero start -> chunk end state (land input zeroed)
 #pragma unroll
                 for (int u = 0; u < U; ++u) st[u][0] = st[u][1] = st[u][2] = L::zero();
-                sweep<ORDER, ADJ, B, true, true, false, false>(cg, dl, len, MASK{}, ml, yl, 0, st);
+                sweep<ORDER, ADJ, B, P, true, true, false, false>(cg, dl, len, MASK{}, ml, yl, 0, st);
 #pragma unroll
                 for (int b = 0; b < B; ++b)
 #pragma unroll
                     for (int q = 0; q < 3; ++q) v[b][q] = L::get(st[b / W][q], b % W);
 #pragma unroll
-                for (int k = 0; k < M; ++k) P[k] = Pc[k];
-                warp_scan<ORDER, false, B>(P, v, lane);
+                for (int k = 0; k < M; ++k) Pm[k] = Pc[k];
+                warp_scan<ORDER, false, B, P>(Pm, v, lane);
                 // ---- B: causal from the true entering state, in place
 #pragma unroll
                 for (int u = 0; u < U; ++u)
@@ -542,23 +553,23 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
                         st[u][q] = L::make(w);
                     }
                 if (maps) {
-                    sweep<ORDER, ADJ, B, true, false, true, true>(cg, dl, len, rebits, ml, yl, rank0, st);
-                    apply_line_tails<ORDER, ADJ, B>(ml, yl, line_re, lane);
+                    sweep<ORDER, ADJ, B, P, true, false, true, true>(cg, dl, len, rebits, ml, yl, rank0, st);
+                    apply_line_tails<ORDER, ADJ, B, P>(ml, yl, line_re, lane);
                 } else {
-                    sweep<ORDER, ADJ, B, true, false, true, false>(cg, dl, len, rebits, ml, yl, rank0, st);
+                    sweep<ORDER, ADJ, B, P, true, false, true, false>(cg, dl, len, rebits, ml, yl, rank0, st);
                 }
                 // ---- C: anticausal from zero at the chunk end
 #pragma unroll
                 for (int u = 0; u < U; ++u) st[u][0] = st[u][1] = st[u][2] = L::zero();
-                if (maps) sweep<ORDER, ADJ, B, false, false, false, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
-                else sweep<ORDER, ADJ, B, false, false, false, false>(cg, dl, len, rebits, ml, yl, 0, st);
+                if (maps) sweep<ORDER, ADJ, B, P, false, false, false, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
+                else sweep<ORDER, ADJ, B, P, false, false, false, false>(cg, dl, len, rebits, ml, yl, 0, st);
 #pragma unroll
                 for (int b = 0; b < B; ++b)
 #pragma unroll
                     for (int q = 0; q < 3; ++q) v[b][q] = L::get(st[b / W][q], b % W);
 #pragma unroll
-                for (int k = 0; k < M; ++k) P[k] = Pa[k];
-                warp_scan<ORDER, true, B>(P, v, lane);
+                for (int k = 0; k < M; ++k) Pm[k] = Pa[k];
+                warp_scan<ORDER, true, B, P>(Pm, v, lane);
                 // ---- D: anticausal from the true entering state, in place
 #pragma unroll
                 for (int u = 0; u < U; ++u)
@@ -569,8 +580,8 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
                         for (int h = 0; h < W; ++h) w[h] = v[u * W + h][q];
                         st[u][q] = L::make(w);
                     }
-                if (maps) sweep<ORDER, ADJ, B, false, false, true, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
-                else sweep<ORDER, ADJ, B, false, false, true, false>(cg, dl, len, rebits, ml, yl, 0, st);
+                if (maps) sweep<ORDER, ADJ, B, P, false, false, true, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
+                else sweep<ORDER, ADJ, B, P, false, false, true, false>(cg, dl, len, rebits, ml, yl, 0, st);
                 __syncwarp();
             }
         };
@@ -638,7 +649,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
             } else if (yr < lines_here) {
                 float *g = dst + (line0 + yr) + (int64_t)yk0 * a.pt_stride;
                 const float *s = db + W * yr * ss;
-                for (int k = yk0; k < n; k += 32, g += row_step) *g = s[W * k];
+                for (int k = yk0; k < n; k += P, g += row_step) *g = s[W * k];
             }
         }
         if (!dbl) __syncthreads();   // stores read the buffer the next copies fill
@@ -646,11 +657,11 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     cp_async_wait_all();   // a CTA without slices still owns its map copies
 }
 
-template <int ORDER, bool ADJ, int R, int B>
-__global__ void __launch_bounds__(32 * R) tile_kernel(TileArgs a)
+template <int ORDER, bool ADJ, int R, int B, int P>
+__global__ void __launch_bounds__(R * P) tile_kernel(TileArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_body<ORDER, ADJ, R, B>(a, blockIdx.x, blockIdx.y, gridDim.y, smem_raw);
+    tile_body<ORDER, ADJ, R, B, P>(a, blockIdx.x, blockIdx.y, gridDim.y, smem_raw);
 }
 
 // Several domains in one launch.  The work list holds, domain after domain,
@@ -669,8 +680,8 @@ struct MultiArgs {
     int ndom;
 };
 
-template <int ORDER, bool ADJ, int R, int B>
-__global__ void __launch_bounds__(32 * R) tile_multi_kernel(const __grid_constant__ MultiArgs m)
+template <int ORDER, bool ADJ, int R, int B, int P>
+__global__ void __launch_bounds__(R * P) tile_multi_kernel(const __grid_constant__ MultiArgs m)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long item_s;
@@ -684,7 +695,7 @@ __global__ void __launch_bounds__(32 * R) tile_multi_kernel(const __grid_constan
         int d = 0;
         while (d + 1 < m.ndom && m.first[d + 1] <= item) ++d;
         const int64_t i = item - m.first[d];
-        tile_body<ORDER, ADJ, R, B>(m.dom[d], i % m.gx[d], i / m.gx[d], m.rows[d], smem_raw);
+        tile_body<ORDER, ADJ, R, B, P>(m.dom[d], i % m.gx[d], i / m.gx[d], m.rows[d], smem_raw);
     }
 }
 

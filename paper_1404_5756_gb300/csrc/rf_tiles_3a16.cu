@@ -1,0 +1,6 @@
+// Tile kernels of the order-3 filter, adjoint steps, 16 lanes per line.
+#include "rf_launch_impl.cuh"
+
+namespace rfvh {
+RF_INSTANTIATE(3, true, 16)
+}  // namespace rfvh
