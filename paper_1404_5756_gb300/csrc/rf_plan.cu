@@ -79,11 +79,13 @@ struct Domain {
 }  // namespace
 
 namespace {
-// Launch shape of one pass of the multi-domain launch for nvar variables.
+// Launch shape of one pass of the multi-domain launch for nvar variables,
+// over the domains whose lines in that direction run with P lanes each.
 struct MultiCfg {
     int64_t nvar;
     bool adjoint;
     int dir;
+    int P;
     TileShape sh;
     size_t smem;
     int occ;
@@ -401,16 +403,20 @@ int64_t smem_stride(int64_t n)
 }
 
 // Lanes per line and chunk length of the tile kernel for line length n.
-// Third-order lines of up to 1008 points take 16 lanes (two lines per warp):
-// chunks of up to 63 points instead of half that, and a scan over 16 lanes
-// (one step fewer, over twice the points), which pays where the 3x3 scans
-// are dear.  The first-order filter keeps 32 lanes: its scans are cheap and
-// its short recursion prefers more, shorter chunks.  C is odd, so the lanes'
-// shared-memory accesses fall in distinct banks.  R = 0 marks lines too long
-// for the tile kernel.
+// Third-order lines of at most kShortLine points take 16 lanes (two lines
+// per warp): chunks of up to 33 points instead of half that, and a scan over
+// 16 lanes (one step fewer, over twice the points).  On short lines the
+// per-chunk work (two 3x3 scans, the re-runs' start, the segment-end
+// records) dominates a 32-lane chunk; from about 500 points on, the halved
+// parallelism of 16 lanes costs more than it saves.  The first-order filter
+// keeps 32 lanes: its scans are cheap.  C is odd, so the lanes' shared-memory
+// accesses fall in distinct banks.  R = 0 marks lines too long for the tile
+// kernel.
+constexpr int64_t kShortLine = 512;
+
 void choose_chunk(Dir &q, int order)
 {
-    q.P = order == 3 && q.n <= 1008 ? 16 : 32;
+    q.P = order == 3 && q.n <= kShortLine ? 16 : 32;
     q.C = (q.n + q.P - 1) / q.P;
     if (q.C % 2 == 0) ++q.C;
     q.R = q.C <= kMaxChunk ? 1 : 0;   // R > 0 marks "tile kernel usable"
@@ -793,7 +799,7 @@ bool multi_try(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, MultiCfg 
     if (!multi_fits(p, dir, nvar, sh, &smem)) return false;
     const int occ = shape_occupancy<ORDER, ADJ, true>(sh, smem);
     if (occ < 1) return false;
-    c = MultiCfg{nvar, ADJ, dir, sh, smem, occ};
+    c = MultiCfg{nvar, ADJ, dir, sh.P, sh, smem, occ};
     return true;
 }
 
@@ -806,20 +812,20 @@ bool multi_try_any(const rf_plan_ *p, int dir, int64_t nvar, bool adjoint, TileS
     return adjoint ? multi_try<1, true>(p, dir, nvar, sh, c) : multi_try<1, false>(p, dir, nvar, sh, c);
 }
 
-// Shape of a pass: tuned, cached, or the first of the direction's preference
-// list that allows two CTAs and eight warps per SM with the largest domain's
-// shared memory (else the first that fits).  occ = 0: no domain of the pass
-// runs on the tile kernel.
-MultiCfg multi_cfg(rf_plan_ *p, int dir, int64_t nvar, bool adjoint)
+// Shape of a pass over the domains with P lanes per line: tuned, cached, or
+// the first of the direction's preference list that allows two CTAs and eight
+// warps per SM with the largest domain's shared memory (else the first that
+// fits).  occ = 0: no domain of the pass runs on the tile kernel with P.
+MultiCfg multi_cfg(rf_plan_ *p, int dir, int64_t nvar, bool adjoint, int P)
 {
     for (const MultiCfg &c : p->mcfg)
-        if (c.nvar == nvar && c.adjoint == adjoint && c.dir == dir) return c;
-    MultiCfg c{nvar, adjoint, dir, {0, 0}, 0, 0};
+        if (c.nvar == nvar && c.adjoint == adjoint && c.dir == dir && c.P == P) return c;
+    MultiCfg c{nvar, adjoint, dir, P, {0, 0, P}, 0, 0};
     bool found = false;
     for (int pass = 0; pass < 2 && !found; ++pass)
         for (const TileShape &sh : dir == 1 ? kShapesY : kShapesX) {
             MultiCfg t;
-            if (multi_try_any(p, dir, nvar, adjoint, sh, t) &&
+            if (sh.P == P && multi_try_any(p, dir, nvar, adjoint, sh, t) &&
                 (pass == 1 || (t.smem <= kSmemTarget && t.occ * sh.R * sh.P / 32 >= 8))) {
                 c = t;
                 found = true;
@@ -830,18 +836,21 @@ MultiCfg multi_cfg(rf_plan_ *p, int dir, int64_t nvar, bool adjoint)
     return c;
 }
 
-// One pass (direction c.dir) over every tile-kernel domain: persistent
-// launches over the work list of up to kMaxMulti domains each.
+// One pass (direction c.dir) over every tile-kernel domain with c.P lanes
+// per line: persistent launches over work lists of at most kMaxMulti domains,
+// the domains split evenly between the launches.
 rf_status multi_pass(rf_plan_ *p, const MultiCfg &c, const float *const *src,
                      float *const *out, int nvar, bool adjoint, cudaStream_t st)
 {
     std::vector<int> doms;
     for (size_t d = 0; d < p->dom.size(); ++d)
-        if (p->dom[d].d[c.dir].R > 0 && p->dom[d].d[c.dir].P == c.sh.P) doms.push_back((int)d);
+        if (p->dom[d].d[c.dir].R > 0 && p->dom[d].d[c.dir].P == c.P) doms.push_back((int)d);
     const int iters = p->opt.order == 3 ? 1 : p->opt.iters;
-    for (size_t c0 = 0; c0 < doms.size(); c0 += kMaxMulti) {
+    const size_t nlaunch = (doms.size() + kMaxMulti - 1) / kMaxMulti;
+    const size_t per = nlaunch ? (doms.size() + nlaunch - 1) / nlaunch : 0;
+    for (size_t c0 = 0; c0 < doms.size(); c0 += per) {
         MultiArgs m{};
-        m.ndom = (int)std::min<size_t>(kMaxMulti, doms.size() - c0);
+        m.ndom = (int)std::min(per, doms.size() - c0);
         m.queue = p->queue;
         int64_t total = 0;
         for (int k = 0; k < m.ndom; ++k) {
@@ -881,18 +890,25 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
                       bool adjoint, bool dry, cudaStream_t st)
 {
     if (!p->queue) RF_TRY(dev_alloc(&p->queue, 1, &p->bytes));
-    MultiCfg cs[2];
-    for (int dir = 0; dir < 2; ++dir) cs[dir] = multi_cfg(p, dir, nvar, adjoint);
-    // domains a pass's multi-domain launch does not cover (lines too long
-    // for the tile kernel, or other lanes per line) launch on their own
-    auto covered = [&](const Dir &q, const MultiCfg &c) {
-        return c.occ > 0 && q.R > 0 && q.P == c.sh.P;
+    // per direction one multi-domain configuration for each lanes-per-line
+    // value (32 and, for the 3rd-RF, 16)
+    const int nP = p->opt.order == 3 ? 2 : 1;
+    MultiCfg cs[2][2];
+    for (int dir = 0; dir < 2; ++dir)
+        for (int k = 0; k < nP; ++k) cs[dir][k] = multi_cfg(p, dir, nvar, adjoint, k ? 16 : 32);
+    // domains no multi-domain launch covers (lines too long for the tile
+    // kernel, or no shape fits) launch on their own
+    auto covered = [&](const Dir &q, int dir) {
+        if (q.R == 0) return false;
+        for (int k = 0; k < nP; ++k)
+            if (cs[dir][k].occ > 0 && cs[dir][k].P == q.P) return true;
+        return false;
     };
     for (Domain &D : p->dom) {
         int64_t nt = 0;
         for (int dir = 0; dir < 2; ++dir) {
             const Dir &q = D.d[dir];
-            if (covered(q, cs[dir])) continue;
+            if (covered(q, dir)) continue;
             if (q.R == 0 || !cfg_of(p, D, dir, nvar, D.g.nz, adjoint).tile)
                 nt = std::max(nt, q.ntail);
         }
@@ -902,13 +918,13 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
     const int K = p->opt.iters;
     for (int pass = 0; pass < 2; ++pass) {
         const int dir = adjoint ? 1 - pass : pass;
-        const MultiCfg &c = cs[dir];
         const float *const *src = pass == 0 ? in : (const float *const *)out;
-        if (c.occ > 0) RF_TRY(multi_pass(p, c, src, out, nvar, adjoint, st));
+        for (int k = 0; k < nP; ++k)
+            if (cs[dir][k].occ > 0) RF_TRY(multi_pass(p, cs[dir][k], src, out, nvar, adjoint, st));
         for (size_t d = 0; d < p->dom.size(); ++d) {
             Domain &D = p->dom[d];
             const Dir &q = D.d[dir];
-            if (covered(q, c)) continue;
+            if (covered(q, dir)) continue;
             const LaunchCfg L = q.R > 0 ? cfg_of(p, D, dir, nvar, D.g.nz, adjoint) : LaunchCfg{};
             if (p->opt.order == 3) {
                 if (adjoint) launch_dir<3, true>(D, q, L, src[d], out[d], nvar, 0, D.g.nz, 1, st);
@@ -1081,34 +1097,37 @@ rf_status tune_multi(rf_plan_ *p, int nvar, cudaEvent_t e0, cudaEvent_t e1, cuda
         cudaEventElapsedTime(ms, e0, e1);
         return RF_OK;
     };
+    const int nP = p->opt.order == 3 ? 2 : 1;
     for (int adj = 0; adj < 2 && s == RF_OK; ++adj)
-        for (int dir = 0; dir < 2 && s == RF_OK; ++dir) {
-            float best_ms = 0.f;
-            MultiCfg best{nvar, adj != 0, dir, {0, 0}, 0, 0};
-            for (const TileShape &sh : kShapesY) {
-                MultiCfg c;
-                if (!multi_try_any(p, dir, nvar, adj != 0, sh, c)) continue;
-                s = multi_pass(p, c, ins.data(), outs.data(), nvar, adj != 0, st);   // warm-up
-                cudaEventRecord(e0, st);
-                for (int r = 0; r < 3 && s == RF_OK; ++r)
-                    s = multi_pass(p, c, ins.data(), outs.data(), nvar, adj != 0, st);
-                float ms = 0.f;
-                if (s == RF_OK) s = elapsed(&ms);
-                if (s != RF_OK) break;
-                if (best_ms == 0.f || ms < best_ms) {
-                    best_ms = ms;
-                    best = c;
+        for (int dir = 0; dir < 2 && s == RF_OK; ++dir)
+            for (int k = 0; k < nP && s == RF_OK; ++k) {
+                const int P = k ? 16 : 32;
+                float best_ms = 0.f;
+                MultiCfg best{nvar, adj != 0, dir, P, {0, 0, P}, 0, 0};
+                for (const TileShape &sh : kShapesY) {
+                    MultiCfg c;
+                    if (sh.P != P || !multi_try_any(p, dir, nvar, adj != 0, sh, c)) continue;
+                    s = multi_pass(p, c, ins.data(), outs.data(), nvar, adj != 0, st);   // warm-up
+                    cudaEventRecord(e0, st);
+                    for (int r = 0; r < 3 && s == RF_OK; ++r)
+                        s = multi_pass(p, c, ins.data(), outs.data(), nvar, adj != 0, st);
+                    float ms = 0.f;
+                    if (s == RF_OK) s = elapsed(&ms);
+                    if (s != RF_OK) break;
+                    if (best_ms == 0.f || ms < best_ms) {
+                        best_ms = ms;
+                        best = c;
+                    }
                 }
+                if (s != RF_OK || best.occ == 0) continue;
+                bool found = false;
+                for (MultiCfg &e : p->mcfg)
+                    if (e.nvar == nvar && e.adjoint == (adj != 0) && e.dir == dir && e.P == P) {
+                        e = best;
+                        found = true;
+                    }
+                if (!found) p->mcfg.push_back(best);
             }
-            if (s != RF_OK || best.occ == 0) continue;
-            bool found = false;
-            for (MultiCfg &e : p->mcfg)
-                if (e.nvar == nvar && e.adjoint == (adj != 0) && e.dir == dir) {
-                    e = best;
-                    found = true;
-                }
-            if (!found) p->mcfg.push_back(best);
-        }
     // multi-domain against per-domain launches
     float t[2] = {0.f, 0.f};
     for (int multi = 0; multi < 2 && s == RF_OK; ++multi) {
@@ -1547,6 +1566,7 @@ rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
         }
     }
     for (const MultiCfg &c : p->mcfg) {
+        if (c.occ == 0) continue;   // no domain of the pass has c.P lanes per line
         std::snprintf(line, sizeof line, "multi-domain %s %s, nvar %lld: R=%d B=%d P=%d smem=%zu CTAs/SM=%d\n",
                       c.dir == 0 ? "x" : "y", c.adjoint ? "adjoint" : "forward", (long long)c.nvar,
                       c.sh.R, c.sh.B, c.sh.P, c.smem, c.occ);

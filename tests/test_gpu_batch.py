@@ -20,10 +20,16 @@ NVAR = 2
 
 def batch():
     """Small ragged domains (seeded recipe of the 64-domain batch, shrunk),
-    one domain whose rows are too long for the tile kernel (4200 points) and
-    one with a mask and length scales that differ per level."""
+    one domain whose rows are too long for the tile kernel (4200 points), one
+    whose rows (1500 points) run with 32 lanes per line where the short lines
+    of the 3rd-RF run with 16, and one with a mask and length scales that
+    differ per level."""
     doms = synth.ragged_domains(6, scale=0.1, max_levels=20)
     rng = np.random.default_rng(55)
+    ny, nx = 8, 1500
+    L = (3.0 + 30.0 * rng.random((ny, nx))).astype(np.float32)
+    m = synth.land_mask(rng, ny, nx, 6.0, 0.2)
+    doms.append(dict(nx=nx, ny=ny, nz=2, mask=m, Lx=L, Ly=L.copy()))
     ny, nx = 12, 4200
     L = (3.0 + 20.0 * rng.random((ny, nx))).astype(np.float32)
     m = (rng.random((ny, nx)) > 0.1).astype(np.uint8)
@@ -74,9 +80,13 @@ def test_multi_domain_launch_equals_separate_plans(data, order, K):
     ts = [torch.from_numpy(x).cuda() for x in xs]
     launches0 = plan.info()[3]
     fwd, adj = plan.apply(ts), plan.apply_adjoint(ts)
-    # two passes, one launch each for the tile domains, plus the long-row
-    # domain's x pass on the line kernel
-    assert plan.info()[3] - launches0 == 2 * 3
+    # per pass one launch for each lanes-per-line group of tile domains (x:
+    # 16 and 32 for the 3rd-RF, 32 for the 1st-RF; y: one group), plus the
+    # long-row domain's x pass on the line kernel
+    assert plan.info()[3] - launches0 == 2 * (4 if order == 3 else 3)
+    text = plan.describe()
+    for dirname in ("x", "y"):
+        assert f"multi-domain {dirname} forward" in text
     for d, t, f, a in zip(doms, ts, fwd, adj):
         single = plan_of([d], order, K)
         assert torch.equal(single.apply(t), f)

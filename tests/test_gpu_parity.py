@@ -310,3 +310,24 @@ def test_long_lines(order, K, nx):
     x = rng.standard_normal((2, 2, ny, nx)).astype(np.float32)
     for adjoint in (False, True):
         assert rel_err(run_gpu(w, x, order, K, adjoint), run_oracle(w, x, order, K, adjoint)) <= TOL
+
+
+@pytest.mark.parametrize("order,K", FILTERS)
+def test_lanes_per_line_switch(order, K):
+    """Third-order lines of up to 512 points run with 16 lanes per line
+    (chunks of 33 points at 512), longer ones with 32 (chunks of 17 at 513);
+    the first-order filter always uses 32.  Rows of 513 and columns of 512
+    points put both kinds in one application."""
+    rng = np.random.default_rng(31)
+    ny, nx = 512, 513
+    mask = (rng.uniform(size=(ny, nx)) > 0.2).astype(np.uint8)
+    L = rng.uniform(2.0, 30.0, (ny, nx)).astype(np.float32)
+    Ly = rng.uniform(2.0, 30.0, (ny, nx)).astype(np.float32)
+    w = dict(mask=mask, Lx=L, Ly=Ly)
+    x = rng.standard_normal((2, 2, ny, nx)).astype(np.float32)
+    for adjoint in (False, True):
+        assert rel_err(run_gpu(w, x, order, K, adjoint), run_oracle(w, x, order, K, adjoint)) <= TOL
+    text = Plan(dict(mask=mask, Lx=L, Ly=Ly, nz=2), Options(order=order, iters=K)).describe()
+    assert "x: lines 512 of 513 points, 32 lanes per line, chunk 17" in text
+    lanes_y = "16 lanes per line, chunk 33" if order == 3 else "32 lanes per line, chunk 17"
+    assert f"y: lines 513 of 512 points, {lanes_y}" in text
