@@ -21,6 +21,8 @@ _LIB = os.path.join(_HERE, "librforacle.so")
 
 NORM_GAUSS_PEAK = 0
 NORM_UNIT_SUM = 1
+COAST_ZERO = 0        # imaginary sea points carry zero (the paper's reading)
+COAST_CONSTANT = 1    # imaginary sea points carry the adjacent sea value
 
 
 def build(force: bool = False) -> str:
@@ -51,9 +53,9 @@ def _load():
         lib.orc_rf3_coeffs.restype = None
         lib.orc_rf1_coeffs.argtypes = [d, i, i, vp, vp]
         lib.orc_rf1_coeffs.restype = None
-        lib.orc_line.argtypes = [i, i, i, d, i, i, i64, vp, vp, vp, vp]
+        lib.orc_line.argtypes = [i, i, i, d, i, i, i, i64, vp, vp, vp, vp]
         lib.orc_line.restype = i
-        lib.orc_vh.argtypes = [i, i, i, d, i, i, i64, i64, i64, i64, vp, i64,
+        lib.orc_vh.argtypes = [i, i, i, d, i, i, i, i64, i64, i64, i64, vp, i64,
                                vp, vp, i64, vp, vp]
         lib.orc_vh.restype = i
         _lib = lib
@@ -92,8 +94,10 @@ def rf1_coeffs(sigma: float, K: int, norm: int = NORM_GAUSS_PEAK):
 
 def line(x, sigma, mask=None, *, order: int = 3, iters: int = 1,
          adjoint: bool = False, img_factor: float = 3.0,
-         norm: int = NORM_GAUSS_PEAK, qcorr: bool = False) -> np.ndarray:
-    """Apply one 1-D filter G (or G^T) to the line x."""
+         norm: int = NORM_GAUSS_PEAK, qcorr: bool = False,
+         coast: int = COAST_ZERO) -> np.ndarray:
+    """Apply one 1-D filter G (or G^T) to the line x.  coast: COAST_ZERO
+    (imaginary points carry zero) or COAST_CONSTANT (the adjacent sea value)."""
     lib = _load()
     x = np.ascontiguousarray(x, dtype=np.float64)
     n = x.shape[0]
@@ -101,7 +105,8 @@ def line(x, sigma, mask=None, *, order: int = 3, iters: int = 1,
     m = (np.ones(n, np.uint8) if mask is None
          else np.ascontiguousarray(mask, dtype=np.uint8))
     out = np.zeros(n)
-    rc = lib.orc_line(order, iters, int(adjoint), float(img_factor), norm, int(bool(qcorr)), n,
+    rc = lib.orc_line(order, iters, int(adjoint), float(img_factor), norm, int(bool(qcorr)),
+                      int(coast), n,
                       _ptr(m), _ptr(sig), _ptr(x), _ptr(out))
     if rc != 0:
         raise ValueError(f"orc_line failed with code {rc}")
@@ -110,7 +115,8 @@ def line(x, sigma, mask=None, *, order: int = 3, iters: int = 1,
 
 def vh(field, mask, Lx, Ly, *, order: int = 3, iters: int = 1,
        adjoint: bool = False, img_factor: float = 3.0,
-       norm: int = NORM_GAUSS_PEAK, qcorr: bool = False) -> np.ndarray:
+       norm: int = NORM_GAUSS_PEAK, qcorr: bool = False,
+       coast: int = COAST_ZERO) -> np.ndarray:
     """V_H = G_y G_x (adjoint: G_x^T G_y^T) on a field [nvar][nz][ny][nx].
 
     field may also be [nz][ny][nx] or [ny][nx]; mask is [mask_nz][ny][nx]
@@ -135,7 +141,7 @@ def vh(field, mask, Lx, Ly, *, order: int = 3, iters: int = 1,
     ly = lev(Ly, np.float64)
     out = np.zeros_like(f)
     rc = lib.orc_vh(order, iters, int(adjoint), float(img_factor), norm, int(bool(qcorr)),
-                    nx, ny, nz, nvar, _ptr(m), m.shape[0], _ptr(lx), _ptr(ly),
+                    int(coast), nx, ny, nz, nvar, _ptr(m), m.shape[0], _ptr(lx), _ptr(ly),
                     lx.shape[0], _ptr(f), _ptr(out))
     if rc != 0:
         raise ValueError(f"orc_vh failed with code {rc}")

@@ -35,6 +35,13 @@
  *    extended segment and only the sea points are read back.  Land output 0.
  *    For K > 1 every iteration re-extends with zeros (imaginary values are not
  *    carried between iterations).
+ *  - Constant-extension coasts (an option; one of the alternative coast
+ *    conditions the Conclusions leave for future work): the imaginary
+ *    points carry the value of the adjacent sea point (the first sea point's
+ *    value on the left, the last one's on the right) instead of zero.  The
+ *    extension E_c is then no longer a zero padding, and its transpose adds
+ *    the adjoint's values at the imaginary points to the edge point they
+ *    copied.
  *  - The 2-D operator V_H = G_y G_x (Sec. 2.2): rows (x) first, then columns
  *    (y), on every level of every variable.
  *  - The adjoint V_H^T = G_x^T G_y^T, written out as the transposed
@@ -195,9 +202,10 @@ static void forward_backward_adjoint(int64_t m, const double *alpha,
     for (int64_t r = 0; r < m; ++r) x[r] *= beta[r];
 }
 
-/* One line of n points.  mask[i] != 0 marks sea.  sig[i] = R_i/dx_i. */
+/* One line of n points.  mask[i] != 0 marks sea.  sig[i] = R_i/dx_i.
+ * coast: 0 imaginary points carry zero, 1 they carry the adjacent sea value. */
 static int line_apply(int order, int iters, int adjoint, double img_factor,
-                      int norm, int qcorr, int64_t n, const uint8_t *mask,
+                      int norm, int qcorr, int coast, int64_t n, const uint8_t *mask,
                       const double *sig, const double *in, double *out,
                       orc_ws *w)
 {
@@ -216,23 +224,35 @@ static int line_apply(int order, int iters, int adjoint, double img_factor,
         fill_coeffs(order, iters, norm, qcorr, sig + b, L, nl, nr, w);
         for (int64_t t = 0; t < L; ++t) out[b + t] = in[b + t];
         for (int k = 0; k < iters; ++k) {
-            /* extend with zeros (E, or R^T for the adjoint) */
+            /* extend (E, or R^T for the adjoint): zeros, or for the forward
+             * constant extension the edge values */
             for (int64_t r = 0; r < m; ++r) w->x[r] = 0.0;
             for (int64_t t = 0; t < L; ++t) w->x[nl + t] = out[b + t];
+            if (coast == 1 && !adjoint) {
+                for (int64_t r = 0; r < nl; ++r) w->x[r] = out[b];
+                for (int64_t r = nl + L; r < m; ++r) w->x[r] = out[b + L - 1];
+            }
             if (adjoint)
                 forward_backward_adjoint(m, w->alpha, w->beta, w->x, w->y);
             else
                 forward_backward(m, w->alpha, w->beta, w->x, w->y);
-            /* restrict to the sea points (R, or E^T for the adjoint) */
+            /* restrict to the sea points (R, or E^T for the adjoint: with
+             * constant extension the imaginary values go to the edge point
+             * they copied) */
             for (int64_t t = 0; t < L; ++t) out[b + t] = w->x[nl + t];
+            if (coast == 1 && adjoint) {
+                for (int64_t r = 0; r < nl; ++r) out[b] += w->x[r];
+                for (int64_t r = nl + L; r < m; ++r) out[b + L - 1] += w->x[r];
+            }
         }
     }
     return ORC_OK;
 }
 
-static int check_opts(int order, int iters, int qcorr)
+static int check_opts(int order, int iters, int qcorr, int coast)
 {
     if (order != 1 && order != 3) return ORC_EINVAL;
+    if (coast != 0 && coast != 1) return ORC_EINVAL;
     if (qcorr && order != 3) return ORC_EINVAL;
     if (iters < 1) return ORC_EINVAL;
     if (order == 3 && iters != 1) return ORC_EINVAL;
@@ -241,12 +261,12 @@ static int check_opts(int order, int iters, int qcorr)
 
 /* Public: one 1-D line (the operator G of one direction). */
 int orc_line(int order, int iters, int adjoint, double img_factor, int norm,
-             int qcorr, int64_t n, const uint8_t *mask, const double *sig,
+             int qcorr, int coast, int64_t n, const uint8_t *mask, const double *sig,
              const double *in, double *out)
 {
-    if (check_opts(order, iters, qcorr) != ORC_OK || n < 0) return ORC_EINVAL;
+    if (check_opts(order, iters, qcorr, coast) != ORC_OK || n < 0) return ORC_EINVAL;
     orc_ws w = {0};
-    int rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr, n, mask, sig,
+    int rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr, coast, n, mask, sig,
                         in, out, &w);
     ws_free(&w);
     return rc;
@@ -257,11 +277,11 @@ int orc_line(int order, int iters, int adjoint, double img_factor, int norm,
  * [L_nz][ny][nx] in grid units; mask_nz and L_nz are 1 (shared by every
  * level) or nz.  in and out may not alias. */
 int orc_vh(int order, int iters, int adjoint, double img_factor, int norm,
-           int qcorr, int64_t nx, int64_t ny, int64_t nz, int64_t nvar,
+           int qcorr, int coast, int64_t nx, int64_t ny, int64_t nz, int64_t nvar,
            const uint8_t *mask, int64_t mask_nz, const double *Lx,
            const double *Ly, int64_t L_nz, const double *in, double *out)
 {
-    if (check_opts(order, iters, qcorr) != ORC_OK) return ORC_EINVAL;
+    if (check_opts(order, iters, qcorr, coast) != ORC_OK) return ORC_EINVAL;
     if (nx < 0 || ny < 0 || nz < 0 || nvar < 0) return ORC_EINVAL;
     if (!(mask_nz == 1 || mask_nz == nz) || !(L_nz == 1 || L_nz == nz))
         return ORC_EINVAL;
@@ -287,7 +307,7 @@ int orc_vh(int order, int iters, int adjoint, double img_factor, int norm,
                 double *b = pass == 0 ? tmp : dst;
                 if (along_x) {
                     for (int64_t j = 0; j < ny && rc == ORC_OK; ++j)
-                        rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr,
+                        rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr, coast,
                                         nx, mk + j * nx, sx + j * nx,
                                         a + j * nx, b + j * nx, &w);
                 } else {
@@ -297,7 +317,7 @@ int orc_vh(int order, int iters, int adjoint, double img_factor, int norm,
                             ls[j] = sy[j * nx + i];
                             li[j] = a[j * nx + i];
                         }
-                        rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr,
+                        rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr, coast,
                                         ny, lm, ls, li, lo, &w);
                         for (int64_t j = 0; j < ny; ++j) b[j * nx + i] = lo[j];
                     }

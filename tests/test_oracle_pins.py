@@ -433,6 +433,133 @@ def test_remark1_valid_bounds(order, K):
     assert np.linalg.norm(err) <= np.abs(eps_h).sum() * np.linalg.norm(s0)
 
 
+# ------------------------------------------- constant-extension coasts
+def dense_const_line_matrix(mask, sig, order=3, K=1, img=3.0, norm=0):
+    """The line operator with constant-extension coasts as a dense matrix:
+    per sea run, E_c copies the first sea value into the ceil(img*sigma)
+    imaginary points on the left and the last one into those on the right,
+    the pair matrix filters the extended run and R reads the sea points
+    back; K iterations give (R G E_c)^K."""
+    n = len(mask)
+    G = np.zeros((n, n))
+    i = 0
+    while i < n:
+        if not mask[i]:
+            i += 1
+            continue
+        b = i
+        while i < n and mask[i]:
+            i += 1
+        seg = list(range(b, i))
+        L = len(seg)
+        nl = int(np.ceil(img * sig[b])) if img > 0 else 0
+        nr = int(np.ceil(img * sig[i - 1])) if img > 0 else 0
+        ext = [sig[b]] * nl + [sig[t] for t in seg] + [sig[i - 1]] * nr
+        E = np.zeros((len(ext), L))
+        E[:nl, 0] = 1.0
+        E[nl + np.arange(L), np.arange(L)] = 1.0
+        E[nl + L:, L - 1] = 1.0
+        R = np.zeros((L, len(ext)))
+        R[np.arange(L), nl + np.arange(L)] = 1.0
+        blk = R @ dense_pair_matrix(ext, order, K, norm) @ E
+        G[np.ix_(seg, seg)] = np.linalg.matrix_power(blk, K)
+    return G
+
+
+@pytest.mark.parametrize("img", [1.0, 2.5])
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 1), (1, 5)])
+def test_constant_coast_matches_dense_extension_matrix(order, K, img):
+    """Constant extension against its definition as matrices, forward and
+    adjoint (the adjoint is the transpose: E_c^T sums the imaginary values
+    into the edge point).  The runs include one of a single point."""
+    rng = np.random.default_rng(17)
+    n = 24
+    mask = np.ones(n, np.uint8)
+    mask[[0, 6, 7, 9, 16]] = 0           # point 8 is a one-point segment
+    sig = rng.uniform(0.6, 3.0, n)
+    G = dense_const_line_matrix(mask, sig, order, K, img)
+    kw = dict(order=order, iters=K, img_factor=img, coast=orc.COAST_CONSTANT)
+    O = oracle_line_matrix(mask, sig, **kw)
+    np.testing.assert_allclose(O, G, rtol=0, atol=1e-12 * np.abs(G).max())
+    OT = oracle_line_matrix(mask, sig, adjoint=True, **kw)
+    np.testing.assert_allclose(OT, G.T, rtol=0, atol=1e-12 * np.abs(G).max())
+    # the zero-input coasts give a different operator
+    assert np.abs(dense_line_matrix(mask, sig, order, K, img) - G).max() > 1e-3
+
+
+def test_constant_coast_equals_padded_line_with_edge_values():
+    """A segment with constant-extension coasts behaves as the same segment
+    inside a longer sea line whose padding holds the edge values (and the
+    coastal length scales), filtered without any imaginary points."""
+    rng = np.random.default_rng(19)
+    L = 37
+    sig = rng.uniform(2.0, 6.0, L)
+    x = rng.standard_normal(L)
+    f = 2.0
+    nl = int(np.ceil(f * sig[0]))
+    nr = int(np.ceil(f * sig[-1]))
+    pad_sig = np.concatenate([[sig[0]] * nl, sig, [sig[-1]] * nr])
+    pad_x = np.concatenate([[x[0]] * nl, x, [x[-1]] * nr])
+    y = orc.line(x, sig, img_factor=f, coast=orc.COAST_CONSTANT)
+    ref = orc.line(pad_x, pad_sig, img_factor=0.0)[nl:nl + L]
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 5)])
+def test_constant_coast_keeps_a_constant_up_to_the_coast(order, K):
+    """A constant field keeps its interior gain sqrt(2 pi) sigma (both
+    filters, Gaussian-peak normalisation) right up to the coast when the
+    imaginary points carry the edge value: with 20 sigma of them the edge
+    transient (decaying like |pole|^distance) is below 1e-6.  With zero
+    input at the imaginary points the coastal value loses about half."""
+    sigma, n = 3.0, 160
+    mask = np.ones(n, np.uint8)
+    mask[70:74] = 0
+    gain = np.sqrt(2 * np.pi) * sigma
+    kw = dict(order=order, iters=K, img_factor=20.0)
+    y = orc.line(np.ones(n), sigma, mask, coast=orc.COAST_CONSTANT, **kw)
+    sea = mask == 1
+    np.testing.assert_allclose(y[sea], gain, rtol=1e-6)
+    assert np.all(y[~sea] == 0.0)
+    y0 = orc.line(np.ones(n), sigma, mask, **kw)
+    assert y0[69] < 0.75 * gain and y0[0] < 0.75 * gain
+
+
+def test_constant_coast_isolated_point_gets_the_line_gain():
+    """One sea point between land: with constant extension the extended run
+    is constant, so the point is multiplied by the 1-D gain sqrt(2 pi) sigma
+    (to the edge transient, below 1e-6 with 20 sigma of imaginary points);
+    without imaginary points it is multiplied by beta^2."""
+    sigma = 2.5
+    mask = np.array([0, 1, 0], np.uint8)
+    x = np.array([4.0, -3.0, 9.0])
+    y = orc.line(x, sigma, mask, img_factor=20.0, coast=orc.COAST_CONSTANT)
+    assert y[1] == pytest.approx(-3.0 * np.sqrt(2 * np.pi) * sigma, rel=1e-6)
+    _, _, beta = orc.rf3_coeffs(sigma)
+    y0 = orc.line(x, sigma, mask, img_factor=0.0, coast=orc.COAST_CONSTANT)
+    assert y0[1] == pytest.approx(-3.0 * beta * beta, rel=1e-14)
+
+
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 5)])
+def test_constant_coast_adjoint_dot_product(order, K):
+    rng = np.random.default_rng(23)
+    nz, ny, nx = 2, 30, 44
+    mask = (rng.uniform(size=(nz, ny, nx)) > 0.25).astype(np.uint8)
+    Lx = rng.uniform(1.0, 9.0, (ny, nx))
+    Ly = rng.uniform(1.0, 9.0, (ny, nx))
+    x = rng.standard_normal((2, nz, ny, nx))
+    y = rng.standard_normal((2, nz, ny, nx))
+    kw = dict(order=order, iters=K, coast=orc.COAST_CONSTANT)
+    Vx = orc.vh(x, mask, Lx, Ly, **kw)
+    VTy = orc.vh(y, mask, Lx, Ly, adjoint=True, **kw)
+    lhs, rhs = np.vdot(Vx, y), np.vdot(x, VTy)
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Vx) * np.linalg.norm(y)
+    # with no imaginary points the two coast treatments coincide exactly
+    a = orc.vh(x, mask, Lx, Ly, img_factor=0.0, **kw)
+    b = orc.vh(x, mask, Lx, Ly, img_factor=0.0, order=order, iters=K)
+    assert np.array_equal(a, b)
+
+
 # ------------------------------------------------------------- validation
 def test_invalid_inputs_rejected():
     with pytest.raises(ValueError):
@@ -443,6 +570,8 @@ def test_invalid_inputs_rejected():
         orc.line(np.ones(5), 2.0, order=3, iters=2)
     with pytest.raises(ValueError):
         orc.line(np.ones(5), 2.0, order=1, iters=5, qcorr=True)
+    with pytest.raises(ValueError):
+        orc.line(np.ones(5), 2.0, coast=2)
     # land points may carry any length scale
     mask = np.array([1, 0, 1, 1, 0], np.uint8)
     sig = np.array([2.0, -5.0, 2.0, 3.0, np.nan])
