@@ -65,8 +65,17 @@ enum {
  * sigma^2, so the filter's variance is sigma^2 instead of about
  * 3.10 sigma + 1.18 sigma^2; the normalisation stays that of sigma (DC gain
  * sqrt(2 pi) sigma per direction).  The number of imaginary points still
- * follows sigma. */
-enum { RF_FLAG_Q_CORRECTED = 1 };
+ * follows sigma.
+ *
+ * RF_FLAG_COAST_CONSTANT (either order, not the paper's coasts): the
+ * imaginary sea points at each end of a sea segment carry the segment's edge
+ * value (its first sea value on the left, its last on the right) instead of
+ * zero -- one of the other coastal boundary conditions the Conclusions leave
+ * for future work.  The adjoint is the exact transpose: the adjoint values
+ * at the imaginary points are added to the edge point they copied.  With
+ * img_factor = 0 (no imaginary points) it changes nothing.  Flags combine
+ * with |. */
+enum { RF_FLAG_Q_CORRECTED = 1, RF_FLAG_COAST_CONSTANT = 2 };
 
 typedef struct rf_plan_ *rf_plan;
 typedef struct rf_graph_ *rf_graph;
@@ -85,7 +94,8 @@ typedef struct {
                              * sigma_coast); 0 = the bare heuristic ICs;
                              must be finite and >= 0                         */
     int norm;             /* RF_NORM_GAUSS_PEAK or RF_NORM_UNIT_SUM          */
-    int flags;            /* 0 or RF_FLAG_Q_CORRECTED (order 3 only)         */
+    int flags;            /* RF_FLAG_Q_CORRECTED (order 3 only) |
+                             RF_FLAG_COAST_CONSTANT, or 0                    */
     int chunk;            /* reserved tuning override, 0 = automatic         */
     int tile;             /* reserved tuning override, 0 = automatic         */
 } rf_options;

@@ -119,4 +119,53 @@ __host__ __device__ inline void tail_map_fp64(double sigma, int n_img, int order
     }
 }
 
+// Vectors of the constant-extension coasts (an option: the imaginary points
+// carry the adjacent sea value instead of zero; one of the other coastal
+// boundary conditions the Conclusions leave for future work).  With A, b, c
+// as above and u_k = sum_{j<k} A^j b the state after k steps of unit input
+// from zero:
+//   head: the n imaginary points before a segment carry its first value x_a,
+//         so the causal state entering the first sea point is x_a s with
+//         s = u_n;
+//   tail: the n imaginary points after a segment carry its last value x_e,
+//         so their forward outputs gain x_e f_k, f_k = c^T u_k, and the
+//         backward start state becomes M X + x_e m with
+//         m = sum_{k=1..n} A^{k-1} b f_k.
+// Order 3 writes 3 entries (delta basis p, d1, d2); order 1 writes v[0].
+__host__ __device__ inline void coast_vectors_fp64(double sigma, int n_img, int order, int K,
+                                                   int norm, bool qc, double *head, double *tail)
+{
+    Coef64 c = coef_fp64(sigma, order, K, norm, qc);
+    for (int r = 0; r < 3; ++r) head[r] = tail[r] = 0.0;
+    if (order == 1) {
+        const double a = 1.0 - c.e;
+        double u = 0.0, v = c.beta;        // u_k, A^{k-1} b
+        for (int k = 1; k <= n_img; ++k) {
+            u = a * u + c.beta;
+            tail[0] += v * u;
+            v *= a;
+        }
+        head[0] = u;
+        return;
+    }
+    const double A[9] = {1.0 - c.e, 1.0 - c.c1, 1.0 - c.c2,
+                         -c.e,      1.0 - c.c1, 1.0 - c.c2,
+                         -c.e,      -c.c1,      1.0 - c.c2};
+    double u[3] = {0.0, 0.0, 0.0};
+    double v[3] = {c.beta, c.beta, c.beta};    // A^{k-1} b
+    for (int k = 1; k <= n_img; ++k) {
+        double nu[3], nv[3];
+        for (int r = 0; r < 3; ++r) {
+            nu[r] = A[3 * r] * u[0] + A[3 * r + 1] * u[1] + A[3 * r + 2] * u[2] + c.beta;
+            nv[r] = A[3 * r] * v[0] + A[3 * r + 1] * v[1] + A[3 * r + 2] * v[2];
+        }
+        for (int r = 0; r < 3; ++r) {
+            u[r] = nu[r];
+            tail[r] += v[r] * u[0];
+        }
+        for (int r = 0; r < 3; ++r) v[r] = nv[r];
+    }
+    for (int r = 0; r < 3; ++r) head[r] = u[r];
+}
+
 }  // namespace rfvh

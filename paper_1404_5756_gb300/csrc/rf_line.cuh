@@ -3,7 +3,11 @@
 // lines whose tile (coefficients, boundary maps, data) does not fit the tile
 // kernel; same coefficients, boundary maps and step functions as the tile
 // kernel.  The anticausal start states of the segment ends go through a
-// global scratch array indexed by slice and boundary-map index.
+// global scratch array indexed by slice and boundary-map index.  With
+// constant-extension coasts (cvec non-null) the causal state entering a
+// segment starts from x_a s and the backward start state gains x_e m
+// (forward); the adjoint adds s.costate and m.lambda to the outputs at the
+// segment's first and last points (see rf_tile.cuh).
 #pragma once
 #include <cstdint>
 
@@ -17,7 +21,9 @@ struct LineArgs {
     const float4 *coef;       // [ncl][nlines][n]
     const int32_t *tail_base; // [ncl*nlines + 1]
     const float2 *tmap;       // [ntail][9] hi/lo pairs
-    float *tscr;              // [nvar*nz][ntail][3]
+    const float4 *cvec;       // [ntail][2] (m, s) of constant-extension coasts, or null
+    float *tscr;              // [nvar*nz][ntail][nr]
+    int nr;                   // floats per record: 3, or 4 with cvec
     int64_t n, nlines, pt_stride, line_stride, plane, ntail, ncl;
     int64_t nz, nvar;         // levels and variables of the field
     int64_t k0, nk;           // this launch filters levels k0 .. k0+nk-1
@@ -36,38 +42,75 @@ __global__ void __launch_bounds__(128) line_kernel(LineArgs a)
     const int64_t base = a.ntail > 0 ? a.tail_base[lev * a.nlines + line] : 0;
     const float *src0 = a.in + slice * a.plane + line * a.line_stride;
     float *out = a.out + slice * a.plane + line * a.line_stride;
-    float *scr = a.tscr + slice * a.ntail * 3;
+    const int nr = a.nr;
+    float *scr = a.tscr + slice * a.ntail * nr;
     const int64_t n = a.n, ps = a.pt_stride;
+    const bool cst = a.cvec != nullptr && a.ntail > 0;
+    const float4 *cv = cst ? a.cvec + 2 * base : nullptr;   // this line's segments
     for (int it = 0; it < a.iters; ++it) {
         const float *src = it == 0 ? src0 : out;
         float st[3] = {0.f, 0.f, 0.f};
         int64_t rk = base;
+        bool prev_sea = false;
         for (int64_t k = 0; k < n; ++k) {
             float4 c = cf[k];
             const bool re = right_end(c);
             c.x = fabsf(c.x);
-            const float x = c.x != 0.f ? src[k * ps] : 0.f;
+            const bool sea = c.x != 0.f;
+            const float x = sea ? src[k * ps] : 0.f;
+            if (!ADJ && cst && sea && !prev_sea) {
+                // a segment starts: rk counts the segments before it
+                const float4 s = cv[2 * (rk - base) + 1];
+                st[0] = x * s.x;
+                st[1] = x * s.y;
+                st[2] = x * s.z;
+            }
+            prev_sea = sea;
             out[k * ps] = step<ORDER, ADJ>(x, c, st);
             if (re && a.ntail > 0) {
-                apply_tail<ORDER, ADJ>(a.tmap + 9 * rk, st, scr + 3 * rk);
+                float *rec = scr + nr * rk;
+                if (cst && ADJ) {
+                    const float4 m = cv[2 * (rk - base)];
+                    rec[3] = ORDER == 3 ? fmaf(m.x, st[0], fmaf(m.y, st[1], m.z * st[2]))
+                                        : m.x * st[0];
+                }
+                apply_tail<ORDER, ADJ>(a.tmap + 9 * rk, st, rec);
+                if (cst && !ADJ) {
+                    const float4 m = cv[2 * (rk - base)];
+                    rec[0] = fmaf(x, m.x, rec[0]);
+                    if (ORDER == 3) {
+                        rec[1] = fmaf(x, m.y, rec[1]);
+                        rec[2] = fmaf(x, m.z, rec[2]);
+                    }
+                }
                 ++rk;
             }
         }
         st[0] = st[1] = st[2] = 0.f;
+        float extra = 0.f;
         for (int64_t k = n - 1; k >= 0; --k) {
             float4 c = cf[k];
+            extra = 0.f;
             if (right_end(c)) {
                 if (a.ntail > 0) {
                     --rk;
-                    st[0] = scr[3 * rk];
-                    st[1] = ORDER == 3 ? scr[3 * rk + 1] : 0.f;
-                    st[2] = ORDER == 3 ? scr[3 * rk + 2] : 0.f;
+                    st[0] = scr[nr * rk];
+                    st[1] = ORDER == 3 ? scr[nr * rk + 1] : 0.f;
+                    st[2] = ORDER == 3 ? scr[nr * rk + 2] : 0.f;
+                    if (cst && ADJ) extra = scr[nr * rk + 3];
                 } else {
                     st[0] = st[1] = st[2] = 0.f;
                 }
                 c.x = fabsf(c.x);
             }
-            out[k * ps] = step<ORDER, ADJ>(out[k * ps], c, st);
+            float y = step<ORDER, ADJ>(out[k * ps], c, st) + extra;
+            if (ADJ && cst && c.x != 0.f && (k == 0 || cf[k - 1].x == 0.f)) {
+                // the segment's first point: rk is its segment's index
+                const float4 s = cv[2 * (rk - base) + 1];
+                y = fmaf(s.x, st[0], y);
+                if (ORDER == 3) y = fmaf(s.y, st[1], fmaf(s.z, st[2], y));
+            }
+            out[k * ps] = y;
         }
     }
 }

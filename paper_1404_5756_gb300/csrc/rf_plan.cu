@@ -24,9 +24,13 @@ using namespace rfvh;
 
 namespace {
 
+// One sea segment of a line: length scale and imaginary points at its end
+// (the boundary map) and at its start (constant-extension coasts).
 struct TailSpec {
     float sigma;
     int n_img;
+    float sigma_h;
+    int n_h;
 };
 
 // How one direction of one domain is launched for a given slice count.
@@ -55,6 +59,8 @@ struct Dir {
     float4 *coef = nullptr;          // [ncl][nlines][n]
     int32_t *tail_base = nullptr;    // [ncl*nlines + 1] first boundary map of each line
     float2 *tmap = nullptr;          // [ntail][9] hi/lo pairs, consecutive along each line
+    float4 *cvec = nullptr;          // [ntail][2] (m, s) of constant-extension coasts
+    bool cst = false;                // constant-extension coasts in force
     int P = 32;                      // lanes per line of the tile kernel (32 or 16)
     float *xfer = nullptr;           // [ncl][nlines][P][XF]
     float4 *coef_il_base = nullptr;  // interleaved coefficients with guards
@@ -131,6 +137,7 @@ void free_domain(Domain &d)
         cudaFree(q.coef);
         cudaFree(q.tail_base);
         cudaFree(q.tmap);
+        cudaFree(q.cvec);
         cudaFree(q.xfer);
         cudaFree(q.coef_il_base);
         cudaFree(q.lanes);
@@ -158,7 +165,9 @@ rf_status check_options(const rf_options &o)
     if (o.iters < 1 || (o.order == 3 && o.iters != 1)) return RF_EINVAL;
     if (!(o.img_factor >= 0.0) || !std::isfinite(o.img_factor)) return RF_EINVAL;
     if (o.norm != RF_NORM_GAUSS_PEAK && o.norm != RF_NORM_UNIT_SUM) return RF_EINVAL;
-    if ((o.flags & ~RF_FLAG_Q_CORRECTED) != 0 || o.chunk < 0 || o.tile < 0) return RF_EINVAL;
+    if ((o.flags & ~(RF_FLAG_Q_CORRECTED | RF_FLAG_COAST_CONSTANT)) != 0 || o.chunk < 0 ||
+        o.tile < 0)
+        return RF_EINVAL;
     if ((o.flags & RF_FLAG_Q_CORRECTED) && o.order != 3) return RF_EINVAL;
     return RF_OK;
 }
@@ -172,6 +181,20 @@ rf_status check_grid(const rf_grid &g)
     if (g.nx > (1 << 30) || g.ny > (1 << 30) || g.nz > 65535) return RF_EINVAL;
     if (g.nx * g.ny > ((int64_t)1 << 40)) return RF_EINVAL;
     return RF_OK;
+}
+
+// Constant-extension coasts in force: the option, and imaginary points to
+// carry the edge values.
+bool plan_cst(const rf_plan_ *p)
+{
+    return (p->opt.flags & RF_FLAG_COAST_CONSTANT) && p->opt.img_factor > 0.0;
+}
+
+// Floats per segment-end record of the kernels: the start state, plus the
+// last input (forward) or the tail-vector term (adjoint) with constant coasts.
+int rec_floats(const Dir &q)
+{
+    return q.cst ? 4 : 3;
 }
 
 rf_status cuda_status(cudaError_t e)
@@ -217,9 +240,12 @@ __global__ void coef_lines_kernel(int64_t ncl, int64_t nx, int64_t ny, int along
 }
 
 // Boundary maps in FP64, stored as hi/lo FP32 pairs (hi = m rounded to
-// FP32, lo = the rest rounded to FP32) for the compensated FP32 application.
+// FP32, lo = the rest rounded to FP32) for the compensated FP32 application;
+// with constant-extension coasts (cvec non-null) also the segment's tail
+// vector m (end) and head vector s (start), FP32.
 __global__ void tail_kernel(int64_t n, const TailSpec *__restrict__ spec,
-                            float2 *__restrict__ tmap, int order, int K, int norm, int qc)
+                            float2 *__restrict__ tmap, float4 *__restrict__ cvec, int order,
+                            int K, int norm, int qc)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -228,6 +254,13 @@ __global__ void tail_kernel(int64_t n, const TailSpec *__restrict__ spec,
     for (int r = 0; r < 9; ++r) {
         const float hi = (float)m[r];
         tmap[9 * i + r] = make_float2(hi, (float)(m[r] - (double)hi));
+    }
+    if (cvec) {
+        double h[3], t[3], unused[3];   // head at the start, tail at the end
+        coast_vectors_fp64((double)spec[i].sigma, spec[i].n_img, order, K, norm, qc != 0, unused, t);
+        coast_vectors_fp64((double)spec[i].sigma_h, spec[i].n_h, order, K, norm, qc != 0, h, unused);
+        cvec[2 * i] = make_float4((float)t[0], (float)t[1], (float)t[2], 0.f);
+        cvec[2 * i + 1] = make_float4((float)h[0], (float)h[1], (float)h[2], 0.f);
     }
 }
 
@@ -256,9 +289,10 @@ __device__ void mm3(const double *P, const double *Q, double *O)
 // Lane-interleaved copy of one direction's coefficients for the tile kernel
 // (step j of lane l of a line at [line][j][l], P lanes per line, points past
 // the line's end are land), with the segment-end flags moved into per-lane
-// bit masks and the rank of each lane's first segment end on its line.  P
-// threads per line; a warp's lines past the end work on the last line (every
-// lane joins the shuffles) and write nothing.
+// bit masks and the rank of each lane's first segment end on its line; the
+// same for the segment starts (a sea point after land or at the line's
+// start).  P threads per line; a warp's lines past the end work on the last
+// line (every lane joins the shuffles) and write nothing.
 __global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C, int P,
                                   const float4 *__restrict__ coef, float4 *__restrict__ il,
                                   LaneInfo *__restrict__ lanes)
@@ -271,10 +305,11 @@ __global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C, int P,
     const int64_t line = ok ? line0 : nlines_total - 1;
     const float4 *src = coef + line * n;
     float4 *dst = il + line * C * P + lane;
-    unsigned long long bits[2] = {0ull, 0ull};
+    unsigned long long bits[2] = {0ull, 0ull}, sbits[2] = {0ull, 0ull};
     for (int j = 0; j < C; ++j) {
         const int64_t k = (int64_t)lane * C + j;
         float4 c = k < n ? src[k] : make_float4(0.f, 0.f, 0.f, -1.f);
+        if (c.x != 0.f && (k == 0 || src[k - 1].x == 0.f)) sbits[j >> 6] |= 1ull << (j & 63);
         if (__float_as_uint(c.x) >> 31) {
             bits[j >> 6] |= 1ull << (j & 63);
             c.x = fabsf(c.x);
@@ -282,16 +317,25 @@ __global__ void interleave_kernel(int64_t nlines_total, int64_t n, int C, int P,
         if (ok) dst[(int64_t)j * P] = c;
     }
     const int nre = __popcll(bits[0]) + __popcll(bits[1]);
-    int incl = nre;
+    const int nrs = __popcll(sbits[0]) + __popcll(sbits[1]);
+    int incl = nre, incs = nrs;
     for (int d = 1; d < P; d <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, d, P);
-        if (lane >= d) incl += t;
+        const int u = __shfl_up_sync(0xffffffffu, incs, d, P);
+        if (lane >= d) {
+            incl += t;
+            incs += u;
+        }
     }
     LaneInfo li;
     li.re.lo = bits[0];
     li.re.hi = bits[1];
     li.rank0 = incl - nre;
     li.nre = nre;
+    li.rs.lo = sbits[0];
+    li.rs.hi = sbits[1];
+    li.rs0 = incs - nrs;
+    li.pad = 0;
     if (ok) lanes[line * P + lane] = li;
 }
 
@@ -342,10 +386,11 @@ int n_imaginary(double img_factor, float sigma)
 }
 
 // Host analysis of one domain: validate length scales at sea points, then
-// for each direction number the segment ends (last sea point of every run of
-// sea points) consecutively along each line, line after line, level after
-// level.  base[d][lev*nlines + line] is the index of a line's first segment
-// end (base has one extra final entry: the total).
+// for each direction number the segments (runs of sea points) consecutively
+// along each line, line after line, level after level, with the length
+// scales and imaginary points at both ends.  base[d][lev*nlines + line] is
+// the index of a line's first segment (base has one extra final entry: the
+// total).
 rf_status analyse(const rf_grid &g, int64_t ncl, const std::vector<uint8_t> &mask,
                   const std::vector<float> &Lx, const std::vector<float> &Ly,
                   double img_factor, std::vector<int32_t> base[2],
@@ -368,10 +413,13 @@ rf_status analyse(const rf_grid &g, int64_t ncl, const std::vector<uint8_t> &mas
         for (int64_t j = 0; j < ny; ++j) {          // x lines: rows
             base[0][(size_t)(k * ny + j)] = (int32_t)sp[0].size();
             int cnt = 0;
+            float sh = 0.f;
             for (int64_t i = 0; i < nx && maps; ++i) {
                 const int64_t p = j * nx + i;
+                if (m[p] && (i == 0 || !m[p - 1])) sh = lx[p];
                 if (m[p] && (i == nx - 1 || !m[p + 1])) {
-                    sp[0].push_back({lx[p], n_imaginary(img_factor, lx[p])});
+                    sp[0].push_back({lx[p], n_imaginary(img_factor, lx[p]), sh,
+                                     n_imaginary(img_factor, sh)});
                     ++cnt;
                 }
             }
@@ -381,10 +429,13 @@ rf_status analyse(const rf_grid &g, int64_t ncl, const std::vector<uint8_t> &mas
         for (int64_t i = 0; i < nx; ++i) {          // y lines: columns
             base[1][(size_t)(k * nx + i)] = (int32_t)sp[1].size();
             int cnt = 0;
+            float sh = 0.f;
             for (int64_t j = 0; j < ny && maps; ++j) {
                 const int64_t p = j * nx + i;
+                if (m[p] && (j == 0 || !m[p - nx])) sh = ly[p];
                 if (m[p] && (j == ny - 1 || !m[p + nx])) {
-                    sp[1].push_back({ly[p], n_imaginary(img_factor, ly[p])});
+                    sp[1].push_back({ly[p], n_imaginary(img_factor, ly[p]), sh,
+                                     n_imaginary(img_factor, sh)});
                     ++cnt;
                 }
             }
@@ -448,6 +499,7 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
     q.line_stride = dir == 0 ? g.nx : 1;
     q.ntail = (int64_t)sp.size();
     q.max_re = max_re;
+    q.cst = (P->opt.flags & RF_FLAG_COAST_CONSTANT) && P->opt.img_factor > 0.0;
     choose_chunk(q, P->opt.order);
     const int64_t plane = g.nx * g.ny, ncl = D.ncl;
     const int o = P->opt.order, K = P->opt.iters, nm = P->opt.norm;
@@ -457,6 +509,7 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
     RF_TRY(dev_alloc(&q.coef, ncl * plane, &P->bytes));
     RF_TRY(dev_alloc(&q.tail_base, (int64_t)base.size(), &P->bytes));
     RF_TRY(dev_alloc(&q.tmap, 9 * q.ntail, &P->bytes));
+    if (q.cst) RF_TRY(dev_alloc(&q.cvec, 2 * q.ntail, &P->bytes));
     if (q.R > 0) {
         RF_TRY(dev_alloc(&q.xfer, ncl * q.nlines * q.P * XS, &P->bytes));
         RF_TRY(dev_alloc(&q.coef_il_base, ncl * q.nlines * q.C * q.P + 2 * kCoefGuard, &P->bytes));
@@ -490,7 +543,7 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
                                                   cudaMemcpyHostToDevice, st));
         if (s == RF_OK) {
             tail_kernel<<<(unsigned)((q.ntail + 127) / 128), 128, 0, st>>>(q.ntail, dsp, q.tmap,
-                                                                           o, K, nm, qc);
+                                                                           q.cvec, o, K, nm, qc);
             s = cuda_status(cudaGetLastError());
         }
         if (s == RF_OK) s = cuda_status(cudaStreamSynchronize(st));
@@ -562,9 +615,10 @@ bool finish_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk, LaunchC
     const int64_t nslices = nvar * nk;
     const int64_t per_cta = D.ncl > 1 ? nvar : nslices;
     if (q.R == 0 || L.sh.P != q.P || (L.sh.B > 1 && L.sh.B > per_cta)) return false;
-    L.smem = (size_t)tile_smem_bytes(L.sh.R, L.sh.B, smem_stride(q.n), q.max_re, L.nbuf);
+    L.smem = (size_t)tile_smem_bytes(L.sh.R, L.sh.B, smem_stride(q.n), q.max_re, L.nbuf,
+                                     rec_floats(q));
     if (L.smem > kSmemMax) return false;
-    L.occ = shape_occupancy<ORDER, ADJ, false>(L.sh, L.smem);
+    L.occ = shape_occupancy<ORDER, ADJ, false>(L.sh, q.cst, L.smem);
     if (L.occ < 1) return false;
     L.tile = true;
     if (D.ncl > 1) {
@@ -589,7 +643,7 @@ LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk)
     for (int pass = 0; pass < 2; ++pass) {
         const size_t cap = pass == 0 ? kSmemTarget : kSmemMax;
         for (const TileShape &s : q.pt_stride != 1 ? kShapesY : kShapesX) {
-            if ((size_t)tile_smem_bytes(s.R, s.B, ss, q.max_re, 1) > cap) continue;
+            if ((size_t)tile_smem_bytes(s.R, s.B, ss, q.max_re, 1, rec_floats(q)) > cap) continue;
             LaunchCfg L;
             L.sh = s;
             L.nbuf = 1;
@@ -659,6 +713,7 @@ TileArgs tile_args(const Domain &D, const Dir &q, const float *in, float *out, i
     a.xfer = q.xfer;
     a.tail_base = q.tail_base;
     a.tmap = q.tmap;
+    a.cvec = q.cst ? q.cvec : nullptr;
     a.n = q.n;
     a.nlines = q.nlines;
     a.C = (int)q.C;
@@ -688,7 +743,7 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
     const int64_t plane = D.g.nx * D.g.ny;
     if (L.tile) {
         const TileArgs a = tile_args(D, q, in, out, nvar, k0, nk, iters, L.nbuf);
-        launch_shape<ORDER, ADJ>(a, L.sh, q.nlines, L.groups, L.smem, st);
+        launch_shape<ORDER, ADJ>(a, L.sh, q.cst, q.nlines, L.groups, L.smem, st);
     } else {
         LineArgs a{};
         a.in = in;
@@ -696,6 +751,8 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
         a.coef = q.coef;
         a.tail_base = q.tail_base;
         a.tmap = q.tmap;
+        a.cvec = q.cst ? q.cvec : nullptr;
+        a.nr = rec_floats(q);
         a.tscr = D.tscr;
         a.n = q.n;
         a.nlines = q.nlines;
@@ -739,7 +796,7 @@ rf_status apply_domain(rf_plan_ *p, Domain &D, const float *in, float *out, int 
         if (!cfg_of(p, D, dir, nvar, nkb, adjoint).tile ||
             !cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint).tile)
             nt = std::max(nt, D.d[dir].ntail);
-    rf_status s = ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 3, &p->bytes);
+    rf_status s = ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 4, &p->bytes);
     if (s != RF_OK) return s;
     const int K = p->opt.iters;
     for (int64_t k0 = 0; k0 < nz; k0 += nkb) {
@@ -785,7 +842,8 @@ bool multi_fits(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, size_t *
     for (const Domain &D : p->dom) {
         const Dir &q = D.d[dir];
         if (q.R == 0 || q.P != sh.P) continue;   // launched on their own
-        m = std::max(m, (size_t)tile_smem_bytes(sh.R, sh.B, smem_stride(q.n), q.max_re, 1));
+        m = std::max(m, (size_t)tile_smem_bytes(sh.R, sh.B, smem_stride(q.n), q.max_re, 1,
+                                                rec_floats(q)));
         any = true;
     }
     *smem = m;
@@ -797,7 +855,7 @@ bool multi_try(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, MultiCfg 
 {
     size_t smem = 0;
     if (!multi_fits(p, dir, nvar, sh, &smem)) return false;
-    const int occ = shape_occupancy<ORDER, ADJ, true>(sh, smem);
+    const int occ = shape_occupancy<ORDER, ADJ, true>(sh, plan_cst(p), smem);
     if (occ < 1) return false;
     c = MultiCfg{nvar, ADJ, dir, sh.P, sh, smem, occ};
     return true;
@@ -867,11 +925,11 @@ rf_status multi_pass(rf_plan_ *p, const MultiCfg &c, const float *const *src,
         const unsigned grid = (unsigned)std::min<int64_t>(total, (int64_t)num_sms() * c.occ);
         RF_TRY(cuda_status(cudaMemsetAsync(p->queue, 0, sizeof(unsigned long long), st)));
         if (p->opt.order == 3) {
-            if (adjoint) launch_multi<3, true>(m, c.sh, grid, c.smem, st);
-            else launch_multi<3, false>(m, c.sh, grid, c.smem, st);
+            if (adjoint) launch_multi<3, true>(m, c.sh, plan_cst(p), grid, c.smem, st);
+            else launch_multi<3, false>(m, c.sh, plan_cst(p), grid, c.smem, st);
         } else {
-            if (adjoint) launch_multi<1, true>(m, c.sh, grid, c.smem, st);
-            else launch_multi<1, false>(m, c.sh, grid, c.smem, st);
+            if (adjoint) launch_multi<1, true>(m, c.sh, plan_cst(p), grid, c.smem, st);
+            else launch_multi<1, false>(m, c.sh, plan_cst(p), grid, c.smem, st);
         }
         const rf_status s = cuda_status(cudaGetLastError());
         if (s != RF_OK) {
@@ -912,7 +970,7 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
             if (q.R == 0 || !cfg_of(p, D, dir, nvar, D.g.nz, adjoint).tile)
                 nt = std::max(nt, q.ntail);
         }
-        RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * D.g.nz * nt * 3, &p->bytes));
+        RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * D.g.nz * nt * 4, &p->bytes));
     }
     if (dry) return RF_OK;
     const int K = p->opt.iters;
@@ -1195,7 +1253,7 @@ rf_status host_pipeline(rf_plan_ *p, Domain &D, const float *in, float *out, int
         if (!cfg_of(p, D, dir, nvar, nkb, adjoint).tile ||
             !cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint).tile)
             nt = std::max(nt, D.d[dir].ntail);
-    RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 3, &p->bytes));
+    RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 4, &p->bytes));
     const size_t pitch = (size_t)(nz * plane) * sizeof(float);
     const int K = p->opt.iters;
     // (a domain's stage is free here: every earlier host-buffer call ended
@@ -1387,7 +1445,8 @@ rf_status rf_apply_static(rf_plan p, const float *const *in, float *const *out, 
         if (!in[d] || !out[d]) return RF_EINVAL;
         const int64_t nslices = (int64_t)nvar * p->dom[d].g.nz;
         for (const Dir &q : p->dom[d].d)
-            if (q.ntail > 0 && nslices * q.ntail * 3 > kStaticScratchFloats) return RF_EINVAL;
+            if (q.ntail > 0 && nslices * q.ntail * rec_floats(q) > kStaticScratchFloats)
+                return RF_EINVAL;
     }
     float *scr = nullptr;
     RF_TRY(static_scratch(&scr));
@@ -1405,6 +1464,8 @@ rf_status rf_apply_static(rf_plan p, const float *const *in, float *const *out, 
             a.coef = q.coef;
             a.tail_base = q.tail_base;
             a.tmap = q.tmap;
+            a.cvec = q.cst ? q.cvec : nullptr;
+            a.nr = rec_floats(q);
             a.tscr = scr;
             a.n = q.n;
             a.nlines = q.nlines;
@@ -1533,6 +1594,11 @@ rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
     if (!p || !buf || cap == 0) return RF_EINVAL;
     std::string t;
     char line[256];
+    std::snprintf(line, sizeof line, "filter: order %d, K %d, img_factor %g, coasts %s%s\n",
+                  p->opt.order, p->opt.iters, p->opt.img_factor,
+                  plan_cst(p) ? "constant extension" : "zero input",
+                  (p->opt.flags & RF_FLAG_Q_CORRECTED) ? ", q-corrected" : "");
+    t += line;
     for (size_t d = 0; d < p->dom.size(); ++d) {
         const Domain &D = p->dom[d];
         std::snprintf(line, sizeof line, "domain %zu: %lld x %lld x %lld, coefficient levels %lld\n", d,

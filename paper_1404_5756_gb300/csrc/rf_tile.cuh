@@ -26,6 +26,14 @@
 //   D  anticausal sweep from the true state -> final output (in place)
 // The forward operator uses the forward steps, the adjoint the transposed
 // steps; the chunk transfer matrices Phi come precomputed from the plan.
+//
+// Constant-extension coasts (CST kernels, an option): the imaginary points
+// carry the segment's edge values.  Forward: at a segment's first sea point
+// the causal state starts from x_a s (A and B), and the backward start state
+// gains x_e m (the last input x_e is recorded with the causal state in B).
+// Adjoint: the transposed terms, s.lambda and m.lambda, are added to the
+// outputs at the segment's first and last points in D.  s and m are
+// per-segment FP32 vectors built in FP64 by the plan.
 #pragma once
 #include <cstdint>
 
@@ -43,6 +51,7 @@ struct Bits64 {
     __device__ __forceinline__ int last() const { return v ? 63 - __clzll((long long)v) : -1; }
     __device__ __forceinline__ void drop_first() { v &= v - 1; }
     __device__ __forceinline__ void drop(int j) { v &= ~(1ull << j); }
+    __device__ __forceinline__ int count() const { return __popcll((long long)v); }
 };
 
 struct SegBits {
@@ -65,13 +74,20 @@ struct SegBits {
         if (j < 64) lo &= ~(1ull << j);
         else hi &= ~(1ull << (j - 64));
     }
+    __device__ __forceinline__ int count() const
+    {
+        return __popcll((long long)lo) + __popcll((long long)hi);
+    }
 };
 
-// Per (line, lane) record of the segment ends in the lane's chunk.
+// Per (line, lane) record of the segment ends and starts in the lane's chunk.
 struct LaneInfo {
     SegBits re;    // segment ends in the chunk
     int rank0;     // segment ends on the line before this chunk
     int nre;       // segment ends in this chunk
+    SegBits rs;    // segment starts (first sea point of a run) in the chunk
+    int rs0;       // segment starts on the line before this chunk
+    int pad;
 };
 
 struct TileArgs {
@@ -82,6 +98,7 @@ struct TileArgs {
     const float *xfer;        // [ncl][nlines][P][XF] chunk transfers
     const int32_t *tail_base; // [ncl*nlines + 1] index of each line's first boundary map
     const float2 *tmap;       // [ntail][9] hi/lo pairs, consecutive along each line
+    const float4 *cvec;       // [ntail][2] (m, s) of constant-extension coasts, or null
     int64_t n, nlines;        // line length, lines per slice
     int64_t pt_stride;        // distance between consecutive points of a line
     int64_t line_stride;      // distance between consecutive lines
@@ -213,14 +230,15 @@ __device__ __forceinline__ void warp_scan(float *Pm, float (*v)[3], int lane)
 
 // Shared-memory bytes of the tile kernel.  Layout: 16-byte guard | maps
 // [R][max_re][9] float2 (padded to 16 bytes) | nbuf data buffers (1 or 2),
-// each [B/W][R][ss] units of W slices | starts [B][R][max_re][3] float |
-// 16-byte guard.  The guards keep the sweeps' one-step-ahead data prefetch
-// (one element past either end of a chunk) inside the allocation.
+// each [B/W][R][ss] units of W slices | starts [B][R][max_re][nr] float
+// (nr = 3, or 4 with constant-extension coasts) | 16-byte guard.  The guards
+// keep the sweeps' one-step-ahead data prefetch (one element past either end
+// of a chunk) inside the allocation.
 __host__ __device__ inline int64_t tile_smem_bytes(int64_t R, int64_t B, int64_t ss,
-                                                   int64_t max_re, int64_t nbuf)
+                                                   int64_t max_re, int64_t nbuf, int64_t nr = 3)
 {
     const int64_t maps = (R * max_re * 9 + 1) / 2 * 2;
-    return 16 + maps * 8 + nbuf * B * R * ss * 4 + B * R * max_re * 12 + 16;
+    return 16 + maps * 8 + nbuf * B * R * ss * 4 + B * R * max_re * nr * 4 + 16;
 }
 
 // B slices per thread travel as U = B/W lane values of W slices each: pairs
@@ -246,29 +264,42 @@ struct LaneT<2> {
 // u's first data element, len points.  CAUSAL walks up, else down.  IN_SEA
 // zeroes the input at land and writes the zero back (first read of the
 // data); WRITE stores the outputs in place.  rebits marks segment ends (bit
-// j <-> point j).  In a causal sweep with TAILS the boundary map turns the
-// state after a segment end into the anticausal start state (stored at
-// ys[b] + 3*rank, rank counting up from rk); in an anticausal sweep the state
-// is reset to that stored start state before the segment end is stepped
-// (rank counting down from rk), or to zero without maps.  Coefficients are
-// fetched two steps ahead and data one step ahead, so memory latency
-// overlaps the arithmetic.
+// j <-> point j).  In a causal sweep with TAILS the state after a segment end
+// is recorded for the boundary map (at ys[b] + NR*rank, rank counting up from
+// rk); in an anticausal sweep the state is reset to the stored start state
+// before the segment end is stepped (rank counting down from rk), or to zero
+// without maps.  Coefficients are fetched two steps ahead and data one step
+// ahead, so memory latency overlaps the arithmetic.
+//
+// CST (constant-extension coasts; the records are NR = 4 floats): rsbits
+// marks segment starts, their vectors (m, s) at cv[2 rank], rank counting up
+// from sk (causal) or down (anticausal).  Forward causal: the state entering
+// a start is x s, and B records the input at a segment end in the fourth
+// float.  Adjoint anticausal with WRITE: the output at a segment end gains
+// the fourth float of its record (m.lambda, from the tails), the output at a
+// start gains s.costate.
 template <int ORDER, bool ADJ, int B, int P, bool CAUSAL, bool IN_SEA, bool WRITE, bool TAILS,
-          class MASK>
+          bool CST, class MASK>
 __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
                                       typename LaneT<Pack<B>::W>::L::T *const *dp, int len,
-                                      MASK rebits, const float2 *ml, float *const *ys, int rk,
+                                      MASK rebits, MASK rsbits, const float4 *__restrict__ cv,
+                                      int sk, float *const *ys, int rk,
                                       typename LaneT<Pack<B>::W>::L::T (*st)[3])
 {
     constexpr int W = Pack<B>::W, U = Pack<B>::U, NS = ORDER == 3 ? 3 : 1;
+    constexpr int NR = CST ? 4 : 3;
+    // start events: forward causal sweeps and the adjoint's writing anticausal one
+    constexpr bool STARTS = CST && (CAUSAL ? !ADJ : (ADJ && WRITE));
+    constexpr bool EXTRA = CST && !CAUSAL && ADJ && WRITE && TAILS;
     using L = typename LaneT<W>::L;
     using T = typename L::T;
     if (len <= 0) return;   // empty chunk: touch no memory
     const int dir = CAUSAL ? 1 : -1;
     int j = CAUSAL ? 0 : len - 1;
-    int re_next;
+    int re_next, rs_next = -2;
     if (CAUSAL) re_next = rebits.first();
     else re_next = rebits.last();
+    if (STARTS) rs_next = CAUSAL ? rsbits.first() : rsbits.last();
     float4 c = __ldg(cp + P * j);
     float4 c1 = __ldg(cp + P * (j + dir));
     T x[U];
@@ -281,19 +312,41 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
 #pragma unroll
         for (int u = 0; u < U; ++u) xn[u] = dp[u][j + dir];
         const bool sea = c.x != 0.f;
-        const CoefV<L> cv(c, sea ? 1.f : 0.f);
+        const CoefV<L> cv4(c, sea ? 1.f : 0.f);
         const bool at_end = j == re_next;
+        const bool at_start = STARTS && j == rs_next;
+        T ex[U];
         if (!CAUSAL && at_end) {
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+            for (int u = 0; u < U; ++u) {
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
                     float v[W];
 #pragma unroll
-                    for (int h = 0; h < W; ++h) v[h] = TAILS ? ys[u * W + h][3 * rk + q] : 0.f;
+                    for (int h = 0; h < W; ++h) v[h] = TAILS ? ys[u * W + h][NR * rk + q] : 0.f;
                     st[u][q] = L::make(v);
                 }
+                if (EXTRA) {
+                    float v[W];
+#pragma unroll
+                    for (int h = 0; h < W; ++h) v[h] = ys[u * W + h][NR * rk + 3];
+                    ex[u] = L::make(v);
+                }
+            }
             if (TAILS) --rk;
+        }
+        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (at_start) sv = __ldg(cv + 2 * sk + 1);
+        if (CAUSAL && at_start) {
+            // the imaginary points before the segment carry its first value
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                st[u][0] = L::mul(x[u], L::bc(sv.x));
+                if (NS == 3) {
+                    st[u][1] = L::mul(x[u], L::bc(sv.y));
+                    st[u][2] = L::mul(x[u], L::bc(sv.z));
+                }
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -302,18 +355,29 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
                 in = L::zero();
                 dp[u][j] = in;
             }
-            const T y = stepv<L, ORDER, ADJ>(in, cv, st[u]);
+            T y = stepv<L, ORDER, ADJ>(in, cv4, st[u]);
+            if (EXTRA && at_end) y = L::add(y, ex[u]);
+            if (!CAUSAL && at_start) {
+                y = L::fma(st[u][0], L::bc(sv.x), y);
+                if (NS == 3) {
+                    y = L::fma(st[u][1], L::bc(sv.y), y);
+                    y = L::fma(st[u][2], L::bc(sv.z), y);
+                }
+            }
             if (WRITE) dp[u][j] = y;
         }
         if (CAUSAL && TAILS && at_end) {
-            // record the final causal state; the boundary maps are applied
-            // afterwards by the whole warp (apply_line_tails)
+            // record the final causal state (and, forward CST, the last
+            // input); the boundary maps are applied afterwards by the whole
+            // warp (apply_line_tails)
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
-                for (int h = 0; h < W; ++h)
+                for (int h = 0; h < W; ++h) {
 #pragma unroll
-                    for (int q = 0; q < NS; ++q) ys[u * W + h][3 * rk + q] = L::get(st[u][q], h);
+                    for (int q = 0; q < NS; ++q) ys[u * W + h][NR * rk + q] = L::get(st[u][q], h);
+                    if (CST && !ADJ) ys[u * W + h][NR * rk + 3] = L::get(x[u], h);
+                }
             ++rk;
         }
         if (at_end) {
@@ -323,6 +387,17 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
             } else {
                 rebits.drop(j);
                 re_next = rebits.last();
+            }
+        }
+        if (at_start) {
+            if (CAUSAL) {
+                rsbits.drop_first();
+                rs_next = rsbits.first();
+                ++sk;
+            } else {
+                rsbits.drop(j);
+                rs_next = rsbits.last();
+                --sk;
             }
         }
         c = c1;
@@ -335,22 +410,41 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
 // Coastal boundary maps of one line, applied by the whole warp after the
 // causal sweep: for every segment end q of the line (its P lanes take
 // q = lane, lane + P, ...) and every slice b, replace the recorded causal state X at
-// ys[b] + 3q by the anticausal start state M_q X (adjoint: M_q^T X).
+// ys[b] + NR q by the anticausal start state M_q X (adjoint: M_q^T X).
 // Spreading the segment ends over the lanes keeps the compensated map
-// arithmetic out of the divergent per-point loop.
-template <int ORDER, bool ADJ, int B, int P>
+// arithmetic out of the divergent per-point loop.  CST: forward adds x_e m_q
+// (x_e recorded in the fourth float), adjoint stores m_q.X in the fourth
+// float for the output at the segment end.
+template <int ORDER, bool ADJ, int B, int P, bool CST>
 __device__ __forceinline__ void apply_line_tails(const float2 *ml, float *const *ys, int nre_line,
-                                                 int lane)
+                                                 int lane, const float4 *__restrict__ cv)
 {
     constexpr int NS = ORDER == 3 ? 3 : 1;
+    constexpr int NR = CST ? 4 : 3;
     __syncwarp();
     for (int q = lane; q < nre_line; q += P) {
+        float4 mv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (CST) mv = __ldg(cv + 2 * q);
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             float X[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < NS; ++k) X[k] = ys[b][3 * q + k];
-            apply_tail<ORDER, ADJ>(ml + 9 * q, X, ys[b] + 3 * q);
+            for (int k = 0; k < NS; ++k) X[k] = ys[b][NR * q + k];
+            float *Y = ys[b] + NR * q;
+            if (CST && ADJ) {
+                float d = mv.x * X[0];
+                if (NS == 3) d = fmaf(mv.y, X[1], fmaf(mv.z, X[2], d));
+                Y[3] = d;
+            }
+            apply_tail<ORDER, ADJ>(ml + 9 * q, X, Y);
+            if (CST && !ADJ) {
+                const float xe = Y[3];
+                Y[0] = fmaf(xe, mv.x, Y[0]);
+                if (NS == 3) {
+                    Y[1] = fmaf(xe, mv.y, Y[1]);
+                    Y[2] = fmaf(xe, mv.z, Y[2]);
+                }
+            }
         }
     }
     __syncwarp();
@@ -359,11 +453,12 @@ __device__ __forceinline__ void apply_line_tails(const float2 *ml, float *const 
 // The work of one CTA: line block bx (lines bx*R ..) and CTA row by of gy
 // rows along the slices (see the slice mapping below).  R*P threads: line rl
 // of the CTA is handled by lanes rl*P .. rl*P + P-1.
-template <int ORDER, bool ADJ, int R, int B, int P>
+template <int ORDER, bool ADJ, int R, int B, int P, bool CST>
 __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t by, int64_t gy,
                                           unsigned char *smem_raw)
 {
     constexpr int XS = XF<ORDER>::size, M = XF<ORDER>::mat;
+    constexpr int NR = CST ? 4 : 3;   // floats per segment-end record
     constexpr int W = Pack<B>::W, U = Pack<B>::U;
     constexpr int LPW = 32 / P;   // lines per warp
     static_assert(P == 32 || P == 16, "lanes per line");
@@ -411,16 +506,23 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     const int ka = min(lane * C, n), kb = min(ka + C, n), len = kb - ka;
     const float4 *cg = a.coef + ((lvl_lines + lc) * C) * P + lane;
     const float2 *ml = ms + rl * mre * 9;
-    SegBits rebits{0ull, 0ull};
-    int rank0 = 0, nre = 0, line_re = 0;
+    SegBits rebits{0ull, 0ull}, rsbits{0ull, 0ull};
+    int rank0 = 0, nre = 0, line_re = 0, rs0 = 0;
+    const float4 *cvl = nullptr;   // the line's constant-coast vectors
     float Pc[M], Pa[M];
     if (active) {
         const LaneInfo li = a.lanes[(lvl_lines + lc) * P + lane];
         rebits = li.re;
         rank0 = li.rank0;
         nre = li.nre;
-        if (mre > 0)
+        if (CST) {
+            rsbits = li.rs;
+            rs0 = li.rs0;
+        }
+        if (mre > 0) {
             line_re = (int)(a.tail_base[lvl_lines + lc + 1] - a.tail_base[lvl_lines + lc]);
+            if (CST) cvl = a.cvec + 2 * (int64_t)a.tail_base[lvl_lines + lc];
+        }
         const float *x = a.xfer + ((lvl_lines + lc) * P + lane) * XS;
         const int oc = ADJ ? 2 : 0, oa = ADJ ? 3 : 1;
 #pragma unroll
@@ -435,7 +537,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     T *dl[U];
     float *yl[B];
 #pragma unroll
-    for (int b = 0; b < B; ++b) yl[b] = ys + (b * R + rl) * mre * 3;
+    for (int b = 0; b < B; ++b) yl[b] = ys + (b * R + rl) * mre * NR;
     // load/store mapping: the x pass copies rows, the y pass R-column
     // strips, thread t owning column r = t % R and rows t / R + P m
     const int yr = threadIdx.x % R, yk0 = threadIdx.x / R;
@@ -525,16 +627,22 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
         if (dbl && gi + g_step < ngroups) issue_loads(gi + g_step, buf ^ 1);
 #pragma unroll
         for (int u = 0; u < U; ++u) dl[u] = dt + ((int64_t)buf * U * R + u * R + rl) * ss + ka;
-        // the filter work of the group, for the chunk's segment-end mask type
-        auto filter = [&](auto rebits) {
+        // the filter work of the group, for the chunk's segment mask type
+        auto filter = [&](auto rebits, auto rsbits) {
             using MASK = decltype(rebits);
+            // constant-extension coasts need boundary maps (imaginary points)
+            const bool cst = CST && maps;
+            const int nrs = CST ? rsbits.count() : 0;
             for (int it = 0; it < a.iters; ++it) {
                 T st[U][3];
                 float v[B][3], Pm[M];
                 // ---- A: causal, zero start -> chunk end state (land input zeroed)
 #pragma unroll
                 for (int u = 0; u < U; ++u) st[u][0] = st[u][1] = st[u][2] = L::zero();
-                sweep<ORDER, ADJ, B, P, true, true, false, false>(cg, dl, len, MASK{}, ml, yl, 0, st);
+                if (cst && !ADJ)
+                    sweep<ORDER, ADJ, B, P, true, true, false, false, CST>(cg, dl, len, MASK{}, rsbits, cvl, rs0, yl, 0, st);
+                else
+                    sweep<ORDER, ADJ, B, P, true, true, false, false, false>(cg, dl, len, MASK{}, MASK{}, nullptr, 0, yl, 0, st);
 #pragma unroll
                 for (int b = 0; b < B; ++b)
 #pragma unroll
@@ -552,17 +660,21 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
                         for (int h = 0; h < W; ++h) w[h] = v[u * W + h][q];
                         st[u][q] = L::make(w);
                     }
-                if (maps) {
-                    sweep<ORDER, ADJ, B, P, true, false, true, true>(cg, dl, len, rebits, ml, yl, rank0, st);
-                    apply_line_tails<ORDER, ADJ, B, P>(ml, yl, line_re, lane);
+                if (cst) {
+                    sweep<ORDER, ADJ, B, P, true, false, true, true, CST>(cg, dl, len, rebits, rsbits, cvl, rs0, yl, rank0, st);
+                    apply_line_tails<ORDER, ADJ, B, P, CST>(ml, yl, line_re, lane, cvl);
+                } else if (maps) {
+                    sweep<ORDER, ADJ, B, P, true, false, true, true, false>(cg, dl, len, rebits, MASK{}, nullptr, 0, yl, rank0, st);
+                    apply_line_tails<ORDER, ADJ, B, P, false>(ml, yl, line_re, lane, nullptr);
                 } else {
-                    sweep<ORDER, ADJ, B, P, true, false, true, false>(cg, dl, len, rebits, ml, yl, rank0, st);
+                    sweep<ORDER, ADJ, B, P, true, false, true, false, false>(cg, dl, len, rebits, MASK{}, nullptr, 0, yl, rank0, st);
                 }
                 // ---- C: anticausal from zero at the chunk end
 #pragma unroll
                 for (int u = 0; u < U; ++u) st[u][0] = st[u][1] = st[u][2] = L::zero();
-                if (maps) sweep<ORDER, ADJ, B, P, false, false, false, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
-                else sweep<ORDER, ADJ, B, P, false, false, false, false>(cg, dl, len, rebits, ml, yl, 0, st);
+                if (cst) sweep<ORDER, ADJ, B, P, false, false, false, true, CST>(cg, dl, len, rebits, MASK{}, cvl, 0, yl, rank0 + nre - 1, st);
+                else if (maps) sweep<ORDER, ADJ, B, P, false, false, false, true, false>(cg, dl, len, rebits, MASK{}, nullptr, 0, yl, rank0 + nre - 1, st);
+                else sweep<ORDER, ADJ, B, P, false, false, false, false, false>(cg, dl, len, rebits, MASK{}, nullptr, 0, yl, 0, st);
 #pragma unroll
                 for (int b = 0; b < B; ++b)
 #pragma unroll
@@ -580,14 +692,15 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
                         for (int h = 0; h < W; ++h) w[h] = v[u * W + h][q];
                         st[u][q] = L::make(w);
                     }
-                if (maps) sweep<ORDER, ADJ, B, P, false, false, true, true>(cg, dl, len, rebits, ml, yl, rank0 + nre - 1, st);
-                else sweep<ORDER, ADJ, B, P, false, false, true, false>(cg, dl, len, rebits, ml, yl, 0, st);
+                if (cst) sweep<ORDER, ADJ, B, P, false, false, true, true, CST>(cg, dl, len, rebits, rsbits, cvl, rs0 + nrs - 1, yl, rank0 + nre - 1, st);
+                else if (maps) sweep<ORDER, ADJ, B, P, false, false, true, true, false>(cg, dl, len, rebits, MASK{}, nullptr, 0, yl, rank0 + nre - 1, st);
+                else sweep<ORDER, ADJ, B, P, false, false, true, false, false>(cg, dl, len, rebits, MASK{}, nullptr, 0, yl, 0, st);
                 __syncwarp();
             }
         };
         if (active) {
-            if (C <= 64) filter(Bits64{rebits.lo});
-            else filter(rebits);
+            if (C <= 64) filter(Bits64{rebits.lo}, Bits64{rsbits.lo});
+            else filter(rebits, rsbits);
         }
         __syncthreads();
         // ---- store
@@ -657,11 +770,11 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
     cp_async_wait_all();   // a CTA without slices still owns its map copies
 }
 
-template <int ORDER, bool ADJ, int R, int B, int P>
+template <int ORDER, bool ADJ, int R, int B, int P, bool CST>
 __global__ void __launch_bounds__(R * P) tile_kernel(TileArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_body<ORDER, ADJ, R, B, P>(a, blockIdx.x, blockIdx.y, gridDim.y, smem_raw);
+    tile_body<ORDER, ADJ, R, B, P, CST>(a, blockIdx.x, blockIdx.y, gridDim.y, smem_raw);
 }
 
 // Several domains in one launch.  The work list holds, domain after domain,
@@ -680,7 +793,7 @@ struct MultiArgs {
     int ndom;
 };
 
-template <int ORDER, bool ADJ, int R, int B, int P>
+template <int ORDER, bool ADJ, int R, int B, int P, bool CST>
 __global__ void __launch_bounds__(R * P) tile_multi_kernel(const __grid_constant__ MultiArgs m)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -695,7 +808,7 @@ __global__ void __launch_bounds__(R * P) tile_multi_kernel(const __grid_constant
         int d = 0;
         while (d + 1 < m.ndom && m.first[d + 1] <= item) ++d;
         const int64_t i = item - m.first[d];
-        tile_body<ORDER, ADJ, R, B, P>(m.dom[d], i % m.gx[d], i / m.gx[d], m.rows[d], smem_raw);
+        tile_body<ORDER, ADJ, R, B, P, CST>(m.dom[d], i % m.gx[d], i / m.gx[d], m.rows[d], smem_raw);
     }
 }
 

@@ -2,5 +2,5 @@
 #include "rf_launch_impl.cuh"
 
 namespace rfvh {
-RF_INSTANTIATE(3, false, 32)
+RF_INSTANTIATE(3, false, 32, false)
 }  // namespace rfvh

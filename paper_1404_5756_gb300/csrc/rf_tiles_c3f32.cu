@@ -1,0 +1,7 @@
+// Tile kernels of the order-3 filter, forward steps, 32 lanes per line,
+// constant-extension coasts.
+#include "rf_launch_impl.cuh"
+
+namespace rfvh {
+RF_INSTANTIATE(3, false, 32, true)
+}  // namespace rfvh

@@ -25,12 +25,16 @@ class Options:
     img_factor: float = 3.0
     norm: int = _lib.RF_NORM_GAUSS_PEAK
     qcorr: bool = False     # q-corrected 3rd-RF: impulse variance sigma^2
+    coast: str = "zero"     # imaginary points carry "zero" or the edge value ("constant")
 
     def to_c(self) -> _lib.rf_options:
+        if self.coast not in ("zero", "constant"):
+            raise ValueError(f"coast must be 'zero' or 'constant', not {self.coast!r}")
         o = _lib.rf_options_default()
         o.order, o.iters = int(self.order), int(self.iters)
         o.img_factor, o.norm = float(self.img_factor), int(self.norm)
-        o.flags = _lib.RF_FLAG_Q_CORRECTED if self.qcorr else 0
+        o.flags = ((_lib.RF_FLAG_Q_CORRECTED if self.qcorr else 0)
+                   | (_lib.RF_FLAG_COAST_CONSTANT if self.coast == "constant" else 0))
         return o
 
 

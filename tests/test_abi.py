@@ -67,8 +67,11 @@ def test_rf_coeffs_rejects_bad_arguments(lib):
         return o
     for o in [with_(order=2), with_(order=3, iters=2), with_(order=1, iters=0),
               with_(img_factor=-1.0), with_(img_factor=float("inf")),
-              with_(img_factor=float("nan")), with_(norm=5), with_(flags=2),
-              with_(order=1, iters=5, flags=_lib.RF_FLAG_Q_CORRECTED)]:
+              with_(img_factor=float("nan")), with_(norm=5), with_(flags=4),
+              with_(flags=_lib.RF_FLAG_COAST_CONSTANT | 8),
+              with_(order=1, iters=5, flags=_lib.RF_FLAG_Q_CORRECTED),
+              with_(order=1, iters=5,
+                    flags=_lib.RF_FLAG_Q_CORRECTED | _lib.RF_FLAG_COAST_CONSTANT)]:
         assert _coeffs(lib, ok_grid, o) == E
 
 
