@@ -484,6 +484,7 @@ def run_gpu(args):
     zh = torch.empty_like(xh).pin_memory()
     for _ in range(2):
         plan3.apply_host(xh, yh, nvar=nvar)
+        plan3.apply_host(yh, zh, nvar=nvar, adjoint=True)
     e2e_steps = max(3, min(args.steps, 10))
     barrier()
     t0 = time.perf_counter()

@@ -1234,7 +1234,7 @@ rf_status host_streams(rf_plan_ *p)
     return RF_OK;
 }
 
-constexpr int64_t kHostBatches = 8;
+constexpr int64_t kHostBatches = 12;
 
 // One domain through host buffers, pipelined over batches of levels: the
 // copy in of a batch (stream s_in), its x and y launches (the caller's

@@ -291,6 +291,9 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
     // start events: forward causal sweeps and the adjoint's writing anticausal one
     constexpr bool STARTS = CST && (CAUSAL ? !ADJ : (ADJ && WRITE));
     constexpr bool EXTRA = CST && !CAUSAL && ADJ && WRITE && TAILS;
+    // a causal sweep that records nothing and starts nothing has no events
+    // (the zero-start sweep A): no per-step test
+    constexpr bool ENDS = !CAUSAL || TAILS;
     using L = typename LaneT<W>::L;
     using T = typename L::T;
     if (len <= 0) return;   // empty chunk: touch no memory
@@ -313,7 +316,7 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
         for (int u = 0; u < U; ++u) xn[u] = dp[u][j + dir];
         const bool sea = c.x != 0.f;
         const CoefV<L> cv4(c, sea ? 1.f : 0.f);
-        const bool at_end = j == re_next;
+        const bool at_end = ENDS && j == re_next;
         const bool at_start = STARTS && j == rs_next;
         T ex[U];
         if (!CAUSAL && at_end) {
