@@ -154,28 +154,47 @@ def make_inputs(levels=None):
     return synth.workload(2, nz=levels)
 
 
-def cpu_oracle_sample(w, seconds: float, order=3, iters=1):
+def cpu_oracle_sample(w, seconds: float, order=3, iters=1, check=None):
     """Time the FP64 oracle (single thread) on whole level slices of the same
-    workload, forward + adjoint per slice, until `seconds` have elapsed."""
+    workload, forward + adjoint per slice, until `seconds` have elapsed.
+    check = (y, z), the GPU's V_h x and V_h^T V_h x of the whole field (host
+    arrays): the oracle's slices are then also compared with them (max
+    |gpu - oracle| / max |oracle| per slice, the worst slice reported)."""
     from oracle import oracle
     mask = w["mask"]
-    L = w["Lx"].astype(np.float64)
+    Lx = w["Lx"].astype(np.float64)
+    Ly = w["Ly"].astype(np.float64)
     x = w["x"]
     nslices = x.shape[0] * x.shape[1]
     done, t0 = 0, time.perf_counter()
+    outs = []
     while True:
         v, k = divmod(done % nslices, x.shape[1])
         s = x[v, k].astype(np.float64)
-        y = oracle.vh(s, mask, L, L, order=order, iters=iters)
-        oracle.vh(y, mask, L, L, order=order, iters=iters, adjoint=True)
+        y = oracle.vh(s, mask, Lx, Ly, order=order, iters=iters)
+        z = oracle.vh(y, mask, Lx, Ly, order=order, iters=iters, adjoint=True)
+        if check is not None and done < nslices:
+            outs.append((v, k, y, z))
         done += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
     pts = done * mask.size
-    return dict(value=2 * pts / el / 1e9, unit="Gpts/s", cores=1, kind="oracle",
-                sample=f"{done} level slices of {w['nx']}x{w['ny']} (fwd+adjoint each), "
-                       f"FP64 oracle, 1 thread, {el:.1f} s")
+    res = dict(value=2 * pts / el / 1e9, unit="Gpts/s", cores=1, kind="oracle",
+               sample=f"{done} level slices of {w['nx']}x{w['ny']} (fwd+adjoint each), "
+                      f"FP64 oracle, 1 thread, {el:.1f} s")
+    if check is not None and outs:
+        gy, gz = check
+
+        def err(g, o):
+            return float(np.abs(g.astype(np.float64) - o).max() / max(np.abs(o).max(), 1e-300))
+        res["parity_sample"] = {
+            "max_rel_err_fwd": max(err(gy[v, k], y) for v, k, y, _ in outs),
+            "max_rel_err_fwd_adj": max(err(gz[v, k], z) for v, k, _, z in outs),
+            "slices": len(outs), "tolerance": 1e-5,
+            "what": "the bench's own V_h x and V_h^T V_h x (tuned launch shapes, full field) "
+                    "against the FP64 oracle on the slices the CPU baseline ran"}
+    return res
 
 
 def run_reference(args):
@@ -519,9 +538,20 @@ def run_gpu(args):
         configs = run_configs(torch, dev, max(3, min(args.steps, 10)), max(args.warmup, 3), peak)
         configs["cg_regional_50k_obs"] = run_cg(torch, dev, w, plan3)
 
+    # the bench's own outputs in the timed launch configuration: the dot test
+    # over the whole field (GPU reductions in FP64), and the slices the CPU
+    # baseline computes compared with the oracle
+    plan3.apply(x, out=y)
+    plan3.apply_adjoint(y, out=z)
+    torch.cuda.synchronize()
+    yy = float((y.double() * y.double()).sum())
+    xz = float((x.double() * z.double()).sum())
+    dot_residual = abs(yy - xz) / max(yy, 1e-300)
+    sea_fraction = float(np.asarray(w["mask"]).astype(bool).mean())
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(w, args.cpu_seconds)
+        cpu = cpu_oracle_sample(w, args.cpu_seconds,
+                                check=(y.cpu().numpy(), z.cpu().numpy()))
 
     line = {
         "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world,
@@ -532,6 +562,11 @@ def run_gpu(args):
                    "points_per_step": 2 * npts, "l2": f"inputs larger than L2 ({4 * npts / 1e6:.0f} MB field)",
                    "parallelism": f"replicas/level batches x{world}"},
         "ms_fwd": float(np.mean(fwd_ms)), "ms_adj": float(np.mean(adj_ms)),
+        "sea_points": {"fraction": sea_fraction, "value": value * sea_fraction,
+                       "unit": "Gpts/s (sea points only)"},
+        "dot_test": {"residual": dot_residual,
+                     "what": "|<Vx, Vx> - <x, V^T V x>| / <Vx, Vx> over the whole field, "
+                             "FP32 operator, FP64 sums", "tolerance": 1e-5},
         "rf1x5": {"value": value1, "unit": "Gpts/s", "ms_per_step": t1_ms / args.steps,
                   "ms_fwd": float(np.mean(f1)), "ms_adj": float(np.mean(a1))},
         "speedup_rf3_over_rf1x5": value / value1,
