@@ -117,8 +117,9 @@ struct TileArgs {
 
 constexpr int kMaxChunk = 128;
 // float4 guard entries before and after the interleaved coefficient array,
-// so the sweeps may prefetch up to two steps past either end of a chunk
-constexpr int kCoefGuard = 64;
+// so the sweeps may prefetch up to three steps past either end of a chunk
+// (3 x 32 lanes)
+constexpr int kCoefGuard = 128;
 
 // Transfer record per chunk: order 3 -> four 3x3 row-major matrices
 // (forward causal, forward anticausal, adjoint causal, adjoint anticausal);
@@ -268,7 +269,7 @@ struct LaneT<2> {
 // is recorded for the boundary map (at ys[b] + NR*rank, rank counting up from
 // rk); in an anticausal sweep the state is reset to the stored start state
 // before the segment end is stepped (rank counting down from rk), or to zero
-// without maps.  Coefficients are fetched two steps ahead and data one step
+// without maps.  Coefficients are fetched three steps ahead and data one step
 // ahead, so memory latency overlaps the arithmetic.
 //
 // CST (constant-extension coasts; the records are NR = 4 floats): rsbits
@@ -305,12 +306,13 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
     if (STARTS) rs_next = CAUSAL ? rsbits.first() : rsbits.last();
     float4 c = __ldg(cp + P * j);
     float4 c1 = __ldg(cp + P * (j + dir));
+    float4 c2 = __ldg(cp + P * (j + 2 * dir));
     T x[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) x[u] = dp[u][j];
 #pragma unroll 2
     for (int t = 0; t < len; ++t, j += dir) {
-        const float4 c2 = __ldg(cp + P * (j + 2 * dir));
+        const float4 c3 = __ldg(cp + P * (j + 3 * dir));
         T xn[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) xn[u] = dp[u][j + dir];
@@ -405,6 +407,7 @@ __device__ __forceinline__ void sweep(const float4 *__restrict__ cp,
         }
         c = c1;
         c1 = c2;
+        c2 = c3;
 #pragma unroll
         for (int u = 0; u < U; ++u) x[u] = xn[u];
     }
