@@ -584,7 +584,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &a, int64_t bx, int64_t
                     const float4 *g1 = s1 ? reinterpret_cast<const float4 *>(s1 + (line0 + r) * a.line_stride)
                                           : nullptr;
                     float4 *sr = reinterpret_cast<float4 *>(db + 2 * r * ss);
-#pragma unroll 4
+#pragma unroll 8
                     for (int q = threadIdx.x; q < n / 4; q += blockDim.x) {
                         const float4 x0 = __ldg(g0 + q);
                         const float4 x1 = g1 ? __ldg(g1 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
