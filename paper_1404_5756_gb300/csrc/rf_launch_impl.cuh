@@ -13,6 +13,22 @@
 namespace rfvh {
 namespace {
 
+// The kernels of one shape: the constant-extension ones are separate
+// templates (their own launch bounds).
+template <int ORDER, bool ADJ, int R, int B, int P, bool CST>
+constexpr auto single_kernel()
+{
+    if constexpr (CST) return &tile_kernel_cst<ORDER, ADJ, R, B, P>;
+    else return &tile_kernel<ORDER, ADJ, R, B, P, false>;
+}
+
+template <int ORDER, bool ADJ, int R, int B, int P, bool CST>
+constexpr auto multi_kernel()
+{
+    if constexpr (CST) return &tile_multi_kernel_cst<ORDER, ADJ, R, B, P>;
+    else return &tile_multi_kernel<ORDER, ADJ, R, B, P, false>;
+}
+
 // Raise a kernel's dynamic shared-memory limit once per device and size, so
 // a launch inside a stream capture makes no attribute call.
 constexpr int kAttrDevices = 64;
@@ -26,10 +42,10 @@ void smem_attr(size_t smem)
     std::lock_guard<std::mutex> lock(mu);
     if (dev >= 0 && dev < kAttrDevices && smem <= done[dev]) return;
     if (MULTI)
-        cudaFuncSetAttribute(tile_multi_kernel<ORDER, ADJ, R, B, P, CST>,
+        cudaFuncSetAttribute(multi_kernel<ORDER, ADJ, R, B, P, CST>(),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else
-        cudaFuncSetAttribute(tile_kernel<ORDER, ADJ, R, B, P, CST>,
+        cudaFuncSetAttribute(single_kernel<ORDER, ADJ, R, B, P, CST>(),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < kAttrDevices) done[dev] = smem;
 }
@@ -40,7 +56,7 @@ void launch_tile(const TileArgs &a, int64_t nlines, int64_t groups, size_t smem,
 {
     smem_attr<ORDER, ADJ, R, B, P, CST, false>(smem);
     dim3 grid((unsigned)((nlines + R - 1) / R), (unsigned)groups);
-    tile_kernel<ORDER, ADJ, R, B, P, CST><<<grid, R * P, smem, st>>>(a);
+    single_kernel<ORDER, ADJ, R, B, P, CST>()<<<grid, R * P, smem, st>>>(a);
 }
 
 template <int ORDER, bool ADJ, int R, int B, int P, bool CST, bool MULTI>
@@ -51,10 +67,10 @@ int tile_occupancy(size_t smem)
     cudaError_t e;
     if (MULTI)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &blocks, tile_multi_kernel<ORDER, ADJ, R, B, P, CST>, R * P, smem);
+            &blocks, multi_kernel<ORDER, ADJ, R, B, P, CST>(), R * P, smem);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &blocks, tile_kernel<ORDER, ADJ, R, B, P, CST>, R * P, smem);
+            &blocks, single_kernel<ORDER, ADJ, R, B, P, CST>(), R * P, smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -66,7 +82,7 @@ template <int ORDER, bool ADJ, int R, int B, int P, bool CST>
 void launch_multi_rb(const MultiArgs &m, unsigned grid, size_t smem, cudaStream_t st)
 {
     smem_attr<ORDER, ADJ, R, B, P, CST, true>(smem);
-    tile_multi_kernel<ORDER, ADJ, R, B, P, CST><<<grid, R * P, smem, st>>>(m);
+    multi_kernel<ORDER, ADJ, R, B, P, CST>()<<<grid, R * P, smem, st>>>(m);
 }
 
 }  // namespace

@@ -783,6 +783,20 @@ __global__ void __launch_bounds__(R * P) tile_kernel(TileArgs a)
     tile_body<ORDER, ADJ, R, B, P, CST>(a, blockIdx.x, blockIdx.y, gridDim.y, smem_raw);
 }
 
+// The constant-extension kernels are compiled for a number of resident CTAs:
+// two for 256 threads (128 registers a thread; their adjoint needs about 170
+// and would otherwise run one CTA per SM), else about 170 registers, what
+// they use anyway.
+template <int R, int P>
+constexpr int kCstMinCtas = R * P >= 256 ? 2 : 65536 / (R * P * 168);
+
+template <int ORDER, bool ADJ, int R, int B, int P>
+__global__ void __launch_bounds__(R * P, (kCstMinCtas<R, P>)) tile_kernel_cst(TileArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_body<ORDER, ADJ, R, B, P, true>(a, blockIdx.x, blockIdx.y, gridDim.y, smem_raw);
+}
+
 // Several domains in one launch.  The work list holds, domain after domain,
 // one item per (line block, CTA row) of that domain's own grid: item i of
 // domain d is line block i % gx[d] and row i / gx[d] of rows[d].  Persistent
@@ -800,9 +814,26 @@ struct MultiArgs {
 };
 
 template <int ORDER, bool ADJ, int R, int B, int P, bool CST>
+__device__ __forceinline__ void multi_body(const MultiArgs &m, unsigned char *smem_raw);
+
+template <int ORDER, bool ADJ, int R, int B, int P, bool CST>
 __global__ void __launch_bounds__(R * P) tile_multi_kernel(const __grid_constant__ MultiArgs m)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    multi_body<ORDER, ADJ, R, B, P, CST>(m, smem_raw);
+}
+
+template <int ORDER, bool ADJ, int R, int B, int P>
+__global__ void __launch_bounds__(R * P, (kCstMinCtas<R, P>))
+    tile_multi_kernel_cst(const __grid_constant__ MultiArgs m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    multi_body<ORDER, ADJ, R, B, P, true>(m, smem_raw);
+}
+
+template <int ORDER, bool ADJ, int R, int B, int P, bool CST>
+__device__ __forceinline__ void multi_body(const MultiArgs &m, unsigned char *smem_raw)
+{
     __shared__ long long item_s;
     const int64_t total = m.first[m.ndom];
     for (;;) {
