@@ -560,6 +560,37 @@ def test_constant_coast_adjoint_dot_product(order, K):
     assert np.array_equal(a, b)
 
 
+# ------------------------------------- comparison with the exact Gaussian
+def test_gaussian_comparison_trends():
+    """The filters approximate exp(-r^2 / 2 sigma^2) (reported, not a parity
+    bar).  What the mathematics fixes: iterating the first-order pair K times
+    approaches the Gaussian as K grows (central limit), the third-order
+    filter approaches it as sigma grows (its variance is 3.10 sigma +
+    1.18 sigma^2, so the linear term fades), and the 2-D impulse response of
+    the 256 x 128 grid at L = 10 sums to at most 2 pi L^2 (the infinite-grid
+    gain), minus what the grid's edges cut off."""
+    def err(order, K, sigma, m):
+        x = np.zeros(m)
+        c = m // 2
+        x[c] = 1.0
+        h = orc.line(x, sigma, order=order, iters=K, img_factor=0.0)
+        g = np.exp(-((np.arange(m) - c) ** 2) / (2 * sigma ** 2))
+        return np.abs(h - g).max()
+    for sigma in (2.0, 10.0):
+        e = [err(1, K, sigma, 301) for K in (1, 5, 10)]
+        assert e[0] > e[1] > e[2]
+    e3 = [err(3, 1, s, m) for s, m in ((2.0, 301), (10.0, 301), (40.0, 801))]
+    assert e3[0] > e3[1] > e3[2]
+    ny, nx = 128, 256
+    x = np.zeros((ny, nx))
+    x[64, 128] = 1.0
+    mask = np.ones((ny, nx), np.uint8)
+    L = np.full((ny, nx), 10.0)
+    for order, K in ((3, 1), (1, 5)):
+        total = orc.vh(x, mask, L, L, order=order, iters=K, img_factor=0.0).sum()
+        assert 0.99 * 2 * np.pi * 100.0 <= total <= 2 * np.pi * 100.0 * (1 + 1e-12)
+
+
 # ------------------------------------------------------------- validation
 def test_invalid_inputs_rejected():
     with pytest.raises(ValueError):
