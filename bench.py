@@ -149,6 +149,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def algorithmic_bytes(nx, ny, nz, nvar):
+    """Algorithmic DRAM bytes of one V_h application: every grid point read
+    and written once (8 B), plus the x and y coefficients (2 x 16 B) and the
+    mask (1 B) per horizontal point."""
+    plane = nx * ny
+    return 8 * nvar * nz * plane + 2 * 16 * plane + plane
+
+
 def make_inputs(levels=None):
     from paper_1404_5756_gb300 import synth
     return synth.workload(2, nz=levels)
@@ -363,7 +371,7 @@ def run_configs(torch, dev, steps, warmup, peak):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
     npts = x.numel()
-    alg = 8 * npts + 33 * w["nx"] * w["ny"]
+    alg = algorithmic_bytes(w["nx"], w["ny"], w["nz"], w["nvar"])
     achieved = alg / (ms / 2 * 1e-3) / 1e9
     out["global_1440x1080x75"] = {"value": 2 * npts / (ms * 1e-3) / 1e9, "unit": "Gpts/s",
                                   "ms_per_step": ms, "points": npts,
@@ -520,9 +528,7 @@ def run_gpu(args):
 
     # ---- roofline of one application (forward) of the dominant operator
     peak, peak_kind = hbm_peak()
-    plane = nx * ny
-    coef_bytes = 2 * 16 * plane + plane          # x and y coefficients + mask
-    alg_bytes = 8 * npts + coef_bytes            # read + write every point once
+    alg_bytes = algorithmic_bytes(nx, ny, nz, nvar)
     t_app = float(np.mean(fwd_ms + adj_ms)) * 1e-3
     achieved = alg_bytes / t_app / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
