@@ -152,7 +152,7 @@ rf_status rf_apply_adjoint(rf_plan p, const float *const *in,
 /* End-to-end variant of rf_apply / rf_apply_adjoint on HOST buffers: copies
  * in[d] (host, ideally pinned) to plan-owned device staging, applies V_H
  * (adjoint != 0: V_H^T), copies the result back into out[d] (host) and
- * synchronises `stream`.  Per domain the work is pipelined over up to 8
+ * synchronises `stream`.  Per domain the work is pipelined over up to 12
  * batches of levels: the copy in of one batch, the filtering of the one
  * before and the copy out of the one before that overlap (two plan-owned
  * copy streams; the kernels run on `stream`).  in[d] and out[d] may be the

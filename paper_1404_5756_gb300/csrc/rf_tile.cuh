@@ -7,7 +7,8 @@
 // boundary maps of the CTA's lines sit in shared memory; the per-point
 // coefficients are read from global memory in a lane-interleaved layout
 // (step j of all P lanes of a line is one contiguous row, so every read is
-// coalesced and stays in L1 across the four sweeps).  The chunk carries are
+// coalesced; the rows are re-read by each sweep and slice group, mostly from
+// L2, three steps ahead of their use).  The chunk carries are
 // resolved with a Kogge-Stone scan of affine maps over the lanes (warp
 // shuffles).  One kernel serves both directions:
 //   x pass: a line is a row, points contiguous in global memory;
@@ -18,9 +19,11 @@
 // K iterations (K = 1 for the third-order filter):
 //   A  causal sweep of every chunk from zero state -> chunk end state
 //   scan of (Phi_chunk, end state) over the lanes -> true state at each chunk
-//   B  causal sweep again from the true state -> causal output (in place);
-//      at the last sea point of a segment the coastal boundary map turns the
-//      final causal state into the anticausal start state (FP64)
+//   B  causal sweep again from the true state -> causal output (in place),
+//      recording the causal state at the last sea point of every segment;
+//      the warp then turns each into the anticausal start state with the
+//      segment's coastal boundary map (built in FP64, applied in compensated
+//      FP32)
 //   C  anticausal sweep from zero state (boundary-map starts included)
 //   scan in the reverse lane order
 //   D  anticausal sweep from the true state -> final output (in place)
