@@ -98,3 +98,33 @@ def test_product_path_has_no_oracle_dependency():
                 text = open(os.path.join(root, f)).read()
                 assert not re.search(r"\boracle\b\s*import|import\s+oracle|from\s+oracle",
                                      text), f
+
+
+def test_python_options_map_to_the_c_flags(lib):
+    """Options -> rf_options: the q-correction and the coast treatment become
+    RF_FLAG_Q_CORRECTED and RF_FLAG_COAST_CONSTANT, and the C header carries
+    the same values the binding uses."""
+    from paper_1404_5756_gb300 import Options
+    hdr = open(_lib.HEADER).read()
+    assert "RF_FLAG_Q_CORRECTED = 1" in hdr and "RF_FLAG_COAST_CONSTANT = 2" in hdr
+    cases = [(dict(), 0), (dict(qcorr=True), _lib.RF_FLAG_Q_CORRECTED),
+             (dict(coast="constant"), _lib.RF_FLAG_COAST_CONSTANT),
+             (dict(qcorr=True, coast="constant"),
+              _lib.RF_FLAG_Q_CORRECTED | _lib.RF_FLAG_COAST_CONSTANT)]
+    for kw, flags in cases:
+        o = Options(**kw).to_c()
+        assert o.flags == flags
+        assert (o.order, o.iters, o.img_factor, o.norm) == (3, 1, 3.0, 0)
+    o = Options(order=1, iters=5, img_factor=2.5, norm=_lib.RF_NORM_UNIT_SUM).to_c()
+    assert (o.order, o.iters, o.img_factor, o.norm, o.flags) == (1, 5, 2.5, 1, 0)
+    with pytest.raises(ValueError):
+        Options(coast="reflect").to_c()
+
+
+def test_plan_refuses_a_cpu_device():
+    torch = pytest.importorskip("torch")
+    from paper_1404_5756_gb300 import Plan
+    mask = torch.ones(4, 5, dtype=torch.uint8)
+    L = torch.full((4, 5), 2.0)
+    with pytest.raises(ValueError):
+        Plan(dict(mask=mask, Lx=L, Ly=L, nz=1), device="cpu")
