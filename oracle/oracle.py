@@ -16,8 +16,11 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "rf_oracle.c")
-_LIB = os.path.join(_HERE, "librforacle.so")
+# RF_ORACLE_SRC / RF_ORACLE_LIB point the shim at another source and library:
+# the mutation test builds copies with planted mistakes this way, to show
+# that the pins catch them.
+_SRC = os.environ.get("RF_ORACLE_SRC") or os.path.join(_HERE, "rf_oracle.c")
+_LIB = os.environ.get("RF_ORACLE_LIB") or os.path.join(_HERE, "librforacle.so")
 
 NORM_GAUSS_PEAK = 0
 NORM_UNIT_SUM = 1
