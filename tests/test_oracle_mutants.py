@@ -54,6 +54,18 @@ MUTANTS = {
     "q-correction solves the wrong quadratic":
         ("return 2.0 * s2 / (B + sqrt(B * B + 4.0 * A * s2));",
          "return 2.0 * s2 / (2.0 * B + sqrt(B * B + 4.0 * A * s2));"),
+    "1st-RF normalisation per iteration instead of per pass":
+        ("1.0 / (4.0 * (double)K));", "1.0 / (2.0 * (double)K));"),
+    "1st-RF coefficient with the wrong root":
+        ("*alpha = 1.0 + E - r;", "*alpha = 1.0 - E + r;"),
+    "land output keeps the input":
+        ("if (!mask[i]) { out[i] = 0.0; ++i; continue; }",
+         "if (!mask[i]) { out[i] = in[i]; ++i; continue; }"),
+    "left imaginary points take the right coast's length scale":
+        ("int64_t src = r < nl ? 0 : (r >= nl + L ? L - 1 : r - nl);",
+         "int64_t src = r < nl ? L - 1 : (r >= nl + L ? L - 1 : r - nl);"),
+    "adjoint forgets the inner beta":
+        ("for (int64_t r = 0; r < m; ++r) z[r] *= beta[r];", "(void)0;"),
 }
 
 
