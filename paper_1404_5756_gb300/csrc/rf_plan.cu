@@ -18,6 +18,7 @@
 #include "rf_coef.cuh"
 #include "rf_launch.h"
 #include "rf_line.cuh"
+#include "rf_reg_launch.h"
 #include "rf_tile.cuh"
 
 using namespace rfvh;
@@ -35,7 +36,8 @@ struct TailSpec {
 
 // How one direction of one domain is launched for a given slice count.
 struct LaunchCfg {
-    bool tile = false;     // tile kernel (else the long-line kernel)
+    bool reg = false;      // register-resident kernel (rf_reg.cuh)
+    bool tile = false;     // tile kernel (else the long-line kernel, unless reg)
     TileShape sh{0, 0};
     size_t smem = 0;
     int occ = 0;           // resident CTAs per SM
@@ -51,6 +53,7 @@ struct CfgEntry {
 
 // Everything one direction (x: rows, y: columns) of one domain needs.
 struct Dir {
+    int dir = 0;                     // 0: x (rows), 1: y (columns)
     int64_t n = 0, nlines = 0;       // line length, lines per slice
     int64_t pt_stride = 0, line_stride = 0;
     int64_t C = 0;                   // chunk length of the tile kernel (odd)
@@ -68,11 +71,19 @@ struct Dir {
     LaneInfo *lanes = nullptr;       // [ncl][nlines][P]
     int64_t ntail = 0;
     int max_re = 0;                  // most segment ends on one line
+    // register-resident kernel (2-D coefficients, zero-input coasts, lines
+    // of at most 1024 points): its chunking and tables
+    RegShape rsh{0, 0};              // C, P; P = 0 marks "not available"
+    float4 *rcoef = nullptr;         // [nlines][C][P] (beta, -e, -c1, -c2), land 0
+    RegLane *rlanes = nullptr;       // [nlines][P]
+    float *rxfer = nullptr;          // [nlines][P][4 * (9 or 1)]
+    int max_ends = 0;                // most segment ends on one line
     std::vector<CfgEntry> cfgs;      // launch shapes chosen so far
 };
 
 struct Domain {
     rf_grid g{};
+    unsigned *status = nullptr;      // the plan's device status word (not owned)
     int64_t ncl = 1;                 // levels with distinct coefficients
     Dir d[2];                        // 0: x, 1: y
     float *tscr = nullptr;           // boundary-map start states
@@ -105,6 +116,7 @@ struct rf_plan_ {
     int64_t launches = 0;
     rf_status sticky = RF_OK;
     unsigned long long *queue = nullptr;   // work-list counter of multi-domain launches
+    unsigned *dstatus = nullptr;           // device status word: bit 0 = a bounded wait gave up
     cudaStream_t s_in = nullptr, s_out = nullptr;   // copy streams of the host-buffer apply
     cudaEvent_t ev_in = nullptr, ev_done = nullptr, ev_out = nullptr;
     std::vector<MultiCfg> mcfg;            // multi-domain launch shapes chosen so far
@@ -141,6 +153,9 @@ void free_domain(Domain &d)
         cudaFree(q.xfer);
         cudaFree(q.coef_il_base);
         cudaFree(q.lanes);
+        cudaFree(q.rcoef);
+        cudaFree(q.rlanes);
+        cudaFree(q.rxfer);
     }
     cudaFree(d.tscr);
     cudaFree(d.stage);
@@ -152,6 +167,8 @@ void free_plan(rf_plan_ *p)
     for (auto &d : p->dom) free_domain(d);
     cudaFree(p->queue);
     p->queue = nullptr;
+    cudaFree(p->dstatus);
+    p->dstatus = nullptr;
     if (p->s_in) cudaStreamDestroy(p->s_in);
     if (p->s_out) cudaStreamDestroy(p->s_out);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
@@ -379,6 +396,95 @@ __global__ void xfer_kernel(int64_t nrec, int64_t n, int64_t C, int P, int order
     }
 }
 
+// Tables of the register-resident kernel for chunks of C points, P lanes per
+// line (rf_reg.cuh), from the line-major coefficients: the interleaved
+// coefficients with land (and points past the line's end) (0, 0, 0, -1), each
+// lane's segment-end, segment-start and land bits with the rank of its first
+// segment end on the line, and the four chunk transfer matrices in FP64
+// products stored as FP32.  A transfer is zero if the chunk holds land (the
+// reset factor clears the state there) or a segment end (the recorded state
+// leaves the line there, and the anticausal start state replaces whatever
+// arrives), and an anticausal-direction one also if it holds a segment
+// start.  Otherwise, with A_k = J - 1 (e, c1, c2)_k the one-step
+// matrix of point k: forward causal A_{b-1}..A_a, forward anticausal
+// A_a..A_{b-1}, adjoint causal (A_a..A_{b-1})^T, adjoint anticausal
+// (A_{b-1}..A_a)^T.  P threads per line; the P threads of a line lie in one
+// warp (P divides 32), and a warp's lines past the end work on the last line
+// and write nothing.
+__global__ void reg_tables_kernel(int64_t nlines, int64_t n, int C, int P, int order,
+                                  const float4 *__restrict__ coef, float4 *__restrict__ rc,
+                                  RegLane *__restrict__ lanes, float *__restrict__ xfer)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t warp_line0 = (t & ~(int64_t)31) / P;
+    if (warp_line0 >= nlines) return;   // whole warps past the end exit together
+    const int64_t line0 = t / P;
+    const int lane = (int)(t % P);
+    const bool ok = line0 < nlines;
+    const int64_t line = ok ? line0 : nlines - 1;
+    const float4 *src = coef + line * n;
+    const int64_t a = (int64_t)lane * C;
+    u64 ends = 0, starts = 0, land = 0;
+    double F[9], Pa[9];
+    for (int k = 0; k < 9; ++k) F[k] = Pa[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    for (int k = 0; k < C; ++k) {
+        const int64_t pos = a + k;
+        float4 c = pos < n ? src[pos] : make_float4(0.f, 0.f, 0.f, -1.f);
+        const bool sea = c.x != 0.f;
+        if (sea && (__float_as_uint(c.x) >> 31)) ends |= 1ull << k;
+        if (sea && (pos == 0 || src[pos - 1].x == 0.f)) starts |= 1ull << k;
+        if (sea) {
+            c.x = fabsf(c.x);
+        } else {
+            land |= 1ull << k;
+            c = make_float4(0.f, 0.f, 0.f, -1.f);   // with g = 0: maps any state to zero
+        }
+        if (ok) rc[(line * C + k) * P + lane] = c;
+        const double e = -(double)c.y, c1 = -(double)c.z, c2 = -(double)c.w;
+        double A[9], T[9];
+        if (order == 3) {
+            const double J[9] = {1, 1, 1, 0, 1, 1, 0, 0, 1};
+            const double kv[3] = {e, c1, c2};
+            for (int r = 0; r < 3; ++r)
+                for (int q = 0; q < 3; ++q) A[3 * r + q] = J[3 * r + q] - kv[q];
+            mm3(A, F, T);
+            for (int q = 0; q < 9; ++q) F[q] = T[q];
+            mm3(Pa, A, T);
+            for (int q = 0; q < 9; ++q) Pa[q] = T[q];
+        } else {
+            F[0] *= 1.0 - e;
+            Pa[0] *= 1.0 - e;
+        }
+    }
+    const bool zc = land != 0 || ends != 0, za = zc || starts != 0;
+    const int M = order == 3 ? 9 : 1;
+    if (ok) {
+        float *o = xfer + (line * P + lane) * (4 * M);
+        for (int k = 0; k < M; ++k) {
+            const int tr = order == 3 ? (k % 3) * 3 + k / 3 : 0;   // transpose index
+            o[k] = zc ? 0.f : (float)F[k];
+            o[M + k] = za ? 0.f : (float)Pa[k];
+            o[2 * M + k] = zc ? 0.f : (float)Pa[tr];
+            o[3 * M + k] = za ? 0.f : (float)F[tr];
+        }
+    }
+    const int nre = __popcll((long long)ends);
+    int incl = nre;
+    for (int d = 1; d < P; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d, P);
+        if (lane >= d) incl += v;
+    }
+    if (ok) {
+        RegLane li;
+        li.ends = ends;
+        li.starts = starts;
+        li.land = land;
+        li.rank0 = incl - nre;
+        li.nre = nre;
+        lanes[line * P + lane] = li;
+    }
+}
+
 int n_imaginary(double img_factor, float sigma)
 {
     if (!(img_factor > 0.0)) return 0;
@@ -394,12 +500,30 @@ int n_imaginary(double img_factor, float sigma)
 rf_status analyse(const rf_grid &g, int64_t ncl, const std::vector<uint8_t> &mask,
                   const std::vector<float> &Lx, const std::vector<float> &Ly,
                   double img_factor, std::vector<int32_t> base[2],
-                  std::vector<TailSpec> sp[2], int max_re[2])
+                  std::vector<TailSpec> sp[2], int max_re[2], int max_ends[2])
 {
     const int64_t nx = g.nx, ny = g.ny, plane = nx * ny;
     base[0].assign((size_t)(ncl * ny + 1), 0);
     base[1].assign((size_t)(ncl * nx + 1), 0);
     max_re[0] = max_re[1] = 0;
+    max_ends[0] = max_ends[1] = 0;
+    // segment ends per line, with or without imaginary points (the register
+    // kernel's record slots)
+    for (int64_t k = 0; k < ncl; ++k) {
+        const uint8_t *m = mask.data() + (g.mask_nz > 1 ? k : 0) * plane;
+        for (int64_t j = 0; j < ny; ++j) {
+            int cnt = 0;
+            for (int64_t i = 0; i < nx; ++i)
+                cnt += m[j * nx + i] && (i == nx - 1 || !m[j * nx + i + 1]);
+            max_ends[0] = std::max(max_ends[0], cnt);
+        }
+        for (int64_t i = 0; i < nx; ++i) {
+            int cnt = 0;
+            for (int64_t j = 0; j < ny; ++j)
+                cnt += m[j * nx + i] && (j == ny - 1 || !m[(j + 1) * nx + i]);
+            max_ends[1] = std::max(max_ends[1], cnt);
+        }
+    }
     for (int64_t k = 0; k < ncl; ++k) {
         const uint8_t *m = mask.data() + (g.mask_nz > 1 ? k : 0) * plane;
         const float *lx = Lx.data() + (g.L_nz > 1 ? k : 0) * plane;
@@ -487,12 +611,33 @@ constexpr TileShape kShapesX[] = {
     {16, 8, 32}, {4, 4, 16},  {8, 4, 16},  {16, 4, 16}, {8, 8, 16},  {16, 8, 16},
     {8, 2, 16},  {16, 2, 16}, {8, 1, 16}};
 
+// Chunking of the register-resident kernel for one direction: P = 32 lanes
+// per line for lines of 513..1024 points, 16 for 257..512, 8 below, and the
+// smallest built chunk length C with P C >= n.  None (P = 0) for per-level
+// coefficients, constant-extension coasts, longer lines, or segment-end
+// records that do not fit shared memory.
+RegShape reg_shape_for(const rf_plan_ *p, const Domain &D, const Dir &q, int dir)
+{
+    if (D.ncl != 1 || plan_cst(p) || q.n > 1024) return RegShape{0, 0};
+    const int P = q.n > 512 ? 32 : q.n > 256 ? 16 : 8;
+    const int64_t need = (q.n + P - 1) / P;
+    RegShape best{0, 0};
+    for (const RegShape &s : kRegShapes)
+        if (s.P == P && s.C >= need && (best.P == 0 || s.C < best.C)) best = s;
+    if (best.P == 0) return best;
+    if (reg_smem_bytes(dir, p->opt.order, best.C, best.P, kRegWarps, q.max_ends, kRegPairs) >
+        (int64_t)kSmemMax)
+        return RegShape{0, 0};
+    return best;
+}
+
 rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
                     const float *L_dev, const std::vector<int32_t> &base,
                     const std::vector<TailSpec> &sp, int max_re, cudaStream_t st)
 {
     const rf_grid &g = D.g;
     Dir &q = D.d[dir];
+    q.dir = dir;
     q.n = dir == 0 ? g.nx : g.ny;
     q.nlines = dir == 0 ? g.ny : g.nx;
     q.pt_stride = dir == 0 ? 1 : g.nx;
@@ -535,6 +680,16 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
             nl, q.n, (int)q.C, q.P, q.coef, q.coef_il, q.lanes);
         RF_TRY(cuda_status(cudaGetLastError()));
     }
+    q.rsh = reg_shape_for(P, D, q, dir);
+    if (q.rsh.P > 0) {
+        const int64_t nrec = q.nlines * q.rsh.P;
+        RF_TRY(dev_alloc(&q.rcoef, nrec * q.rsh.C, &P->bytes));
+        RF_TRY(dev_alloc(&q.rlanes, nrec, &P->bytes));
+        RF_TRY(dev_alloc(&q.rxfer, nrec * 4 * (o == 3 ? 9 : 1), &P->bytes));
+        reg_tables_kernel<<<(unsigned)((nrec + 127) / 128), 128, 0, st>>>(
+            q.nlines, q.n, q.rsh.C, q.rsh.P, o, q.coef, q.rcoef, q.rlanes, q.rxfer);
+        RF_TRY(cuda_status(cudaGetLastError()));
+    }
     if (!sp.empty()) {
         TailSpec *dsp = nullptr;
         int64_t dummy = 0;
@@ -571,8 +726,10 @@ rf_status build_domain(rf_plan_ *P, Domain &D, const uint8_t *mask_dev,
     for (auto &v : hm) v = v ? 1 : 0;
     std::vector<int32_t> base[2];
     std::vector<TailSpec> sp[2];
-    int max_re[2];
-    RF_TRY(analyse(g, D.ncl, hm, hx, hy, P->opt.img_factor, base, sp, max_re));
+    int max_re[2], max_ends[2];
+    RF_TRY(analyse(g, D.ncl, hm, hx, hy, P->opt.img_factor, base, sp, max_re, max_ends));
+    D.d[0].max_ends = max_ends[0];
+    D.d[1].max_ends = max_ends[1];
     RF_TRY(build_dir(P, D, 0, mask_dev, Lx_dev, base[0], sp[0], max_re[0], st));
     RF_TRY(build_dir(P, D, 1, mask_dev, Ly_dev, base[1], sp[1], max_re[1], st));
     return cuda_status(cudaStreamSynchronize(st));
@@ -633,12 +790,34 @@ bool finish_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk, LaunchC
     return true;
 }
 
-// Default (untuned) tile shape: the first shape in the direction's
-// preference list whose single-buffered shared memory allows two CTAs per
-// SM, else the first that fits at all; the long-line kernel if none does.
+// Configuration of the register-resident kernel for one pass of nvar
+// variables and nk levels, if the direction has its tables and the grid fits.
+template <int ORDER, bool ADJ>
+bool reg_cfg(const Dir &q, int64_t nvar, int64_t nk, LaunchCfg &L)
+{
+    if (q.rsh.P == 0) return false;
+    const int64_t ngroups = (nvar * nk + 2 * kRegPairs - 1) / (2 * kRegPairs);
+    if ((q.dir == 0 ? (ngroups + kRegWarps - 1) / kRegWarps : ngroups) > 65535) return false;
+    L = LaunchCfg{};
+    L.reg = true;
+    L.smem = (size_t)reg_smem_bytes(q.dir, ORDER, q.rsh.C, q.rsh.P, kRegWarps, q.max_ends,
+                                    kRegPairs);
+    L.occ = q.dir == 0 ? reg_occupancy<ORDER, ADJ, 0>(q.rsh, L.smem)
+                       : reg_occupancy<ORDER, ADJ, 1>(q.rsh, L.smem);
+    return L.occ > 0;
+}
+
+// Default (untuned) configuration: the register-resident kernel where it
+// applies; else the first tile shape in the direction's preference list
+// whose single-buffered shared memory allows two CTAs per SM, else the
+// first that fits at all; the long-line kernel if none does.
 template <int ORDER, bool ADJ>
 LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk)
 {
+    {
+        LaunchCfg L;
+        if (reg_cfg<ORDER, ADJ>(q, nvar, nk, L)) return L;
+    }
     const int64_t ss = smem_stride(q.n);
     for (int pass = 0; pass < 2; ++pass) {
         const size_t cap = pass == 0 ? kSmemTarget : kSmemMax;
@@ -659,6 +838,16 @@ std::vector<LaunchCfg> launch_candidates(const Domain &D, const Dir &q, int64_t 
                                          int64_t nk)
 {
     std::vector<LaunchCfg> out;
+    {
+        // where the register kernel applies it is the only candidate: the
+        // kernel (hence the arithmetic) depends on the line length and the
+        // options alone, never on tuning
+        LaunchCfg L;
+        if (reg_cfg<ORDER, ADJ>(q, nvar, nk, L)) {
+            out.push_back(L);
+            return out;
+        }
+    }
     for (const TileShape &s : kShapesY)
         for (int nbuf = 1; nbuf <= 2; ++nbuf) {
             LaunchCfg L;
@@ -741,7 +930,32 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
                 float *out, int64_t nvar, int64_t k0, int64_t nk, int iters, cudaStream_t st)
 {
     const int64_t plane = D.g.nx * D.g.ny;
-    if (L.tile) {
+    if (L.reg) {
+        RegArgs a{};
+        a.in = in;
+        a.out = out;
+        a.coef = q.rcoef;
+        a.lanes = q.rlanes;
+        a.xfer = q.rxfer;
+        a.tail_base = q.tail_base;
+        a.tmap = q.ntail > 0 ? q.tmap : nullptr;
+        a.n = q.n;
+        a.nlines = q.nlines;
+        a.nx = D.g.nx;
+        a.plane = plane;
+        a.nz = D.g.nz;
+        a.k0 = k0;
+        a.nk = nk;
+        a.nslices = nvar * nk;
+        a.ngroups = (a.nslices + 2 * kRegPairs - 1) / (2 * kRegPairs);
+        a.max_re = q.max_ends;
+        a.vec4 = D.g.nx % 4 == 0 && ((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0;
+        a.iters = iters;
+        a.zero = 0;
+        a.status = D.status;
+        if (q.dir == 0) reg_launch<ORDER, ADJ, 0>(a, q.rsh, L.smem, st);
+        else reg_launch<ORDER, ADJ, 1>(a, q.rsh, L.smem, st);
+    } else if (L.tile) {
         const TileArgs a = tile_args(D, q, in, out, nvar, k0, nk, iters, L.nbuf);
         launch_shape<ORDER, ADJ>(a, L.sh, q.cst, q.nlines, L.groups, L.smem, st);
     } else {
@@ -771,6 +985,13 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
     }
 }
 
+// True if a configuration runs the long-line kernel (which keeps its
+// segment-end states in the domain's global scratch).
+bool line_path(const LaunchCfg &L)
+{
+    return !L.tile && !L.reg;
+}
+
 // Launch configuration of direction dir for nvar variables and batches of
 // nk levels: the tuned or cached one, else the default.
 LaunchCfg cfg_of(const rf_plan_ *p, Domain &D, int dir, int64_t nvar, int64_t nk, bool adjoint)
@@ -793,8 +1014,8 @@ rf_status apply_domain(rf_plan_ *p, Domain &D, const float *in, float *out, int 
     // global scratch for segment-end states, only for the long-line path
     int64_t nt = 0;
     for (int dir = 0; dir < 2; ++dir)
-        if (!cfg_of(p, D, dir, nvar, nkb, adjoint).tile ||
-            !cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint).tile)
+        if (line_path(cfg_of(p, D, dir, nvar, nkb, adjoint)) ||
+            line_path(cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint)))
             nt = std::max(nt, D.d[dir].ntail);
     rf_status s = ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 4, &p->bytes);
     if (s != RF_OK) return s;
@@ -841,7 +1062,7 @@ bool multi_fits(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, size_t *
     bool any = false;
     for (const Domain &D : p->dom) {
         const Dir &q = D.d[dir];
-        if (q.R == 0 || q.P != sh.P) continue;   // launched on their own
+        if (q.R == 0 || q.P != sh.P || q.rsh.P > 0) continue;   // launched on their own
         m = std::max(m, (size_t)tile_smem_bytes(sh.R, sh.B, smem_stride(q.n), q.max_re, 1,
                                                 rec_floats(q)));
         any = true;
@@ -902,7 +1123,8 @@ rf_status multi_pass(rf_plan_ *p, const MultiCfg &c, const float *const *src,
 {
     std::vector<int> doms;
     for (size_t d = 0; d < p->dom.size(); ++d)
-        if (p->dom[d].d[c.dir].R > 0 && p->dom[d].d[c.dir].P == c.P) doms.push_back((int)d);
+        if (p->dom[d].d[c.dir].R > 0 && p->dom[d].d[c.dir].P == c.P && p->dom[d].d[c.dir].rsh.P == 0)
+            doms.push_back((int)d);
     const int iters = p->opt.order == 3 ? 1 : p->opt.iters;
     const size_t nlaunch = (doms.size() + kMaxMulti - 1) / kMaxMulti;
     const size_t per = nlaunch ? (doms.size() + nlaunch - 1) / nlaunch : 0;
@@ -957,7 +1179,7 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
     // domains no multi-domain launch covers (lines too long for the tile
     // kernel, or no shape fits) launch on their own
     auto covered = [&](const Dir &q, int dir) {
-        if (q.R == 0) return false;
+        if (q.R == 0 || q.rsh.P > 0) return false;   // register-kernel domains launch on their own
         for (int k = 0; k < nP; ++k)
             if (cs[dir][k].occ > 0 && cs[dir][k].P == q.P) return true;
         return false;
@@ -967,7 +1189,7 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
         for (int dir = 0; dir < 2; ++dir) {
             const Dir &q = D.d[dir];
             if (covered(q, dir)) continue;
-            if (q.R == 0 || !cfg_of(p, D, dir, nvar, D.g.nz, adjoint).tile)
+            if (q.R == 0 || line_path(cfg_of(p, D, dir, nvar, D.g.nz, adjoint)))
                 nt = std::max(nt, q.ntail);
         }
         RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * D.g.nz * nt * 4, &p->bytes));
@@ -1250,8 +1472,8 @@ rf_status host_pipeline(rf_plan_ *p, Domain &D, const float *in, float *out, int
     const int64_t nkb = (nz + kHostBatches - 1) / kHostBatches;
     int64_t nt = 0;   // scratch of the long-line kernel
     for (int dir = 0; dir < 2; ++dir)
-        if (!cfg_of(p, D, dir, nvar, nkb, adjoint).tile ||
-            !cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint).tile)
+        if (line_path(cfg_of(p, D, dir, nvar, nkb, adjoint)) ||
+            line_path(cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint)))
             nt = std::max(nt, D.d[dir].ntail);
     RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 4, &p->bytes));
     const size_t pitch = (size_t)(nz * plane) * sizeof(float);
@@ -1355,8 +1577,17 @@ rf_status rf_coeffs(const rf_grid *grids, int ndomains, const uint8_t *const *ma
     P->opt = o;
     P->dom.resize((size_t)ndomains);
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        rf_status s = dev_alloc(&P->dstatus, 1, &P->bytes);
+        if (s == RF_OK) s = cuda_status(cudaMemsetAsync(P->dstatus, 0, sizeof(unsigned), st));
+        if (s != RF_OK) {
+            rf_plan_destroy(P);
+            return s;
+        }
+    }
     for (int d = 0; d < ndomains; ++d) {
         P->dom[d].g = grids[d];
+        P->dom[d].status = P->dstatus;
         rf_status s = build_domain(P, P->dom[d], mask[d], Lx[d], Ly[d], st);
         if (s != RF_OK) {
             rf_plan_destroy(P);
@@ -1616,8 +1847,20 @@ rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
                           dir == 0 ? "x" : "y", (long long)q.nlines, (long long)q.n, q.P, (long long)q.C,
                           (long long)q.ntail);
             t += line;
+            if (q.rsh.P > 0) {
+                std::snprintf(line, sizeof line,
+                              "    register kernel: chunk %d, %d lanes per line, record slots %d\n",
+                              q.rsh.C, q.rsh.P, q.max_ends);
+                t += line;
+            }
             for (const CfgEntry &e : q.cfgs) {
-                if (e.cfg.tile)
+                if (e.cfg.reg)
+                    std::snprintf(line, sizeof line,
+                                  "    nvar %lld, %lld levels, %s: register kernel C=%d P=%d smem=%zu "
+                                  "CTAs/SM=%d\n",
+                                  (long long)e.nvar, (long long)e.nk, e.adjoint ? "adjoint" : "forward",
+                                  q.rsh.C, q.rsh.P, e.cfg.smem, e.cfg.occ);
+                else if (e.cfg.tile)
                     std::snprintf(line, sizeof line,
                                   "    nvar %lld, %lld levels, %s: tile R=%d B=%d P=%d buffers=%d smem=%zu "
                                   "CTAs/SM=%d rows=%lld\n",
@@ -1652,6 +1895,16 @@ rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
 rf_status rf_plan_status(rf_plan p)
 {
     if (!p) return RF_EINVAL;
+    if (p->sticky == RF_OK && p->dstatus) {
+        // the kernels' device-side status (a bounded wait that gave up)
+        unsigned w = 0;
+        if (cudaMemcpy(&w, p->dstatus, sizeof w, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            p->sticky = RF_ECUDA;
+        } else if (w & 1u) {
+            p->sticky = RF_ETIMEOUT;
+        }
+    }
     return p->sticky;
 }
 

@@ -1,0 +1,6 @@
+// Register-resident kernel of the third-order filter, adjoint (transposed) steps, x pass (rows).
+#include "rf_reg_impl.cuh"
+
+namespace rfvh {
+RF_REG_INSTANTIATE(3, true, 0)
+}  // namespace rfvh

@@ -1,0 +1,61 @@
+// rf_reg_launch.h -- launch entry points of the register-resident kernel
+// (rf_reg.cuh).  It is instantiated per filter order, forward/adjoint and
+// direction in eight translation units (rf_reg_*.cu) that compile in
+// parallel; each holds the (chunk length, lanes per line) pairs below.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "rf_reg.cuh"
+
+namespace rfvh {
+
+constexpr int kRegWarps = 4;   // warps per CTA
+constexpr int kRegPairs = 2;   // slice pairs per thread (4 slices)
+
+struct RegShape {
+    int C, P;   // chunk length, lanes per line
+};
+
+// Built (C, P) pairs.  The planner takes P = 32 for lines of 513..1024
+// points, 16 for 257..512 and 8 up to 256, and the smallest built C with
+// P C >= n.
+constexpr RegShape kRegShapes[] = {{24, 32}, {32, 32}, {24, 16}, {32, 16}, {16, 8}, {32, 8}};
+
+// Launch one pass.  Returns false if (C, P) is not built.
+template <int ORDER, bool ADJ, int DIR>
+bool reg_launch(const RegArgs &a, RegShape sh, size_t smem, cudaStream_t st);
+
+// Resident CTAs per SM with `smem` bytes of dynamic shared memory (0: cannot
+// run or not built).
+template <int ORDER, bool ADJ, int DIR>
+int reg_occupancy(RegShape sh, size_t smem);
+
+#define RF_REG_DECLARE(O, A, D)                                                              \
+    extern template bool reg_launch<O, A, D>(const RegArgs &, RegShape, size_t, cudaStream_t); \
+    extern template int reg_occupancy<O, A, D>(RegShape, size_t);
+RF_REG_DECLARE(3, false, 0)
+RF_REG_DECLARE(3, false, 1)
+RF_REG_DECLARE(3, true, 0)
+RF_REG_DECLARE(3, true, 1)
+RF_REG_DECLARE(1, false, 0)
+RF_REG_DECLARE(1, false, 1)
+RF_REG_DECLARE(1, true, 0)
+RF_REG_DECLARE(1, true, 1)
+#undef RF_REG_DECLARE
+
+// Grid of a pass: x: (row blocks of 32/P rows, slice groups / warps per
+// CTA); y: (column blocks of kRegWarps * 32/P columns, slice groups).
+inline dim3 reg_grid(int dir, RegShape sh, int64_t nlines, int64_t ngroups)
+{
+    const int64_t lpw = 32 / sh.P;
+    if (dir == 0)
+        return dim3((unsigned)((nlines + lpw - 1) / lpw),
+                    (unsigned)((ngroups + kRegWarps - 1) / kRegWarps));
+    const int64_t R = kRegWarps * lpw;
+    return dim3((unsigned)((nlines + R - 1) / R), (unsigned)ngroups);
+}
+
+}  // namespace rfvh

@@ -1,6 +1,7 @@
 """Ragged multi-domain batches: one persistent launch per pass over a work
-list of every domain's (line block, slice group) items, and CUDA graphs of a
-whole application.  Parity with the FP64 oracle per domain (bar 1e-5 of the
+list of the tile-kernel domains' (line block, slice group) items (domains on
+the register kernel launch on their own), and CUDA graphs of a whole
+application.  Parity with the FP64 oracle per domain (bar 1e-5 of the
 domain's max |oracle|); the multi-domain launch, separate per-domain plans,
 tuned shapes and graph replays must agree bit for bit, since none of them
 changes the arithmetic of a slice."""
@@ -43,6 +44,29 @@ def batch():
     return doms, xs
 
 
+def expected_launches(doms, order):
+    """Kernel launches of one application of the batch: per pass, one for
+    every domain whose lines (at most 1024 points, coefficients shared by
+    all levels) run on the register kernel, one for every domain on the
+    long-line kernel (lines over 4064 points), and one multi-domain launch
+    per lanes-per-line group of the remaining tile-kernel domains (16 lanes
+    for third-order lines of at most 512 points, else 32)."""
+    n = 0
+    for along_x in (True, False):
+        groups = set()
+        for d in doms:
+            shared = np.asarray(d["mask"]).ndim == 2 and np.asarray(d["Lx"]).ndim == 2
+            m = d["nx"] if along_x else d["ny"]
+            if shared and m <= 1024:
+                n += 1
+            elif m > 4064:
+                n += 1
+            else:
+                groups.add(16 if order == 3 and m <= 512 else 32)
+        n += len(groups)
+    return n
+
+
 def plan_of(doms, order, K):
     return Plan([dict(mask=d["mask"], Lx=d["Lx"], Ly=d["Ly"], nz=d["nz"]) for d in doms],
                 Options(order=order, iters=K))
@@ -80,10 +104,7 @@ def test_multi_domain_launch_equals_separate_plans(data, order, K):
     ts = [torch.from_numpy(x).cuda() for x in xs]
     launches0 = plan.info()[3]
     fwd, adj = plan.apply(ts), plan.apply_adjoint(ts)
-    # per pass one launch for each lanes-per-line group of tile domains (x:
-    # 16 and 32 for the 3rd-RF, 32 for the 1st-RF; y: one group), plus the
-    # long-row domain's x pass on the line kernel
-    assert plan.info()[3] - launches0 == 2 * (4 if order == 3 else 3)
+    assert plan.info()[3] - launches0 == 2 * expected_launches(doms, order)
     text = plan.describe()
     for dirname in ("x", "y"):
         assert f"multi-domain {dirname} forward" in text

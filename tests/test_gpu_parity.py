@@ -279,8 +279,9 @@ def test_autograd_backward_is_adjoint_and_matches_finite_differences():
 
 
 def test_tuned_shapes_give_identical_results():
-    """The autotuner only changes lines per CTA, slices per thread and
-    buffering, never the arithmetic of a slice: results are bit-identical."""
+    """The autotuner only changes launch shapes and level batches, never the
+    kernel of a direction or the arithmetic of a slice: results are
+    bit-identical."""
     w = synth.workload(2, nz=3, nvar=2)
     x = torch.from_numpy(w["x"]).cuda()
     for order, K in FILTERS:
@@ -291,7 +292,7 @@ def test_tuned_shapes_give_identical_results():
         assert torch.equal(plan.apply_adjoint(x), ref_a)
         assert plan.status() == 0
         text = plan.describe()
-        assert "x: lines 384 of 1024 points" in text and "tile R=" in text
+        assert "x: lines 384 of 1024 points" in text and "register kernel C=32 P=32" in text
 
 
 @pytest.mark.parametrize("order,K", FILTERS)
