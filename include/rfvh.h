@@ -92,12 +92,19 @@ typedef struct {
     int iters;            /* K: must be 1 for order 3, >= 1 for order 1      */
     double img_factor;    /* imaginary points per coast end = ceil(img_factor
                              * sigma_coast); 0 = the bare heuristic ICs;
-                             must be finite and >= 0                         */
+                             +INFINITY = the infinite imaginary sea (the
+                             closed-form limit of the boundary map, zero-input
+                             coasts only: with RF_FLAG_COAST_CONSTANT it gives
+                             RF_EUNSUPPORTED); must be >= 0, not NaN          */
     int norm;             /* RF_NORM_GAUSS_PEAK or RF_NORM_UNIT_SUM          */
     int flags;            /* RF_FLAG_Q_CORRECTED (order 3 only) |
                              RF_FLAG_COAST_CONSTANT, or 0                    */
-    int chunk;            /* reserved tuning override, 0 = automatic         */
-    int tile;             /* reserved tuning override, 0 = automatic         */
+    int chunk;            /* chunk-length override: must be 0 (automatic);
+                             any other value gives RF_EUNSUPPORTED, since the
+                             kernels derive the chunking from the line length */
+    int tile;             /* tile-shape override: must be 0 (automatic, or the
+                             autotuner's choice); other values give
+                             RF_EUNSUPPORTED                                  */
 } rf_options;
 
 /* Fill *opt with the defaults: order 3, iters 1, img_factor 3, Gaussian-peak
@@ -119,9 +126,13 @@ rf_status rf_options_default(rf_options *opt);
  * forward state at each segment's last sea point to the backward start state
  * (the effect of the n_img imaginary points).  The caller's mask and length
  * scale buffers may be freed once the call returns.
+ * The map of the infinite imaginary sea (img_factor = +INFINITY) is the
+ * limit sum_{j>=0} A^j Q A^j of the finite one, solved in FP64 as its Stein
+ * equation M = Q + A M A.
  * Errors: RF_EINVAL (null pointers, ndomains < 1, nx/ny/nz < 1, mask_nz or
  * L_nz not in {1, nz}, bad options, invalid length scale at a sea point),
- * RF_ENOMEM, RF_ECUDA. */
+ * RF_EUNSUPPORTED (non-zero chunk or tile override; infinite imaginary sea
+ * with constant-extension coasts), RF_ENOMEM, RF_ECUDA. */
 rf_status rf_coeffs(const rf_grid *grids, int ndomains,
                     const uint8_t *const *mask, const float *const *Lx,
                     const float *const *Ly, const rf_options *opt,

@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
         return _LIB
     tmp = _LIB + f".{os.getpid()}.tmp"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off",
-                           "-fno-fast-math", "-fPIC", "-shared", _SRC,
+                           "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", _SRC,
                            "-o", tmp, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
@@ -61,12 +61,28 @@ def _load():
         lib.orc_vh.argtypes = [i, i, i, d, i, i, i, i64, i64, i64, i64, vp, i64,
                                vp, vp, i64, vp, vp]
         lib.orc_vh.restype = i
+        lib.orc_n_imaginary.argtypes = [d, d]
+        lib.orc_n_imaginary.restype = i64
+        lib.orc_set_threads.argtypes = [i]
+        lib.orc_set_threads.restype = i
         _lib = lib
     return _lib
 
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def n_imaginary(img_factor: float, sigma: float) -> int:
+    """Imaginary points the oracle puts at a coast of length scale sigma
+    (img_factor = inf: the cut of the infinite imaginary sea)."""
+    return int(_load().orc_n_imaginary(float(img_factor), float(sigma)))
+
+
+def set_threads(n: int) -> int:
+    """Threads of vh()'s loop over (variable, level) slices (OpenMP; 1 by
+    default).  Results do not depend on it."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def q_of_sigma(sigma: float) -> float:

@@ -34,7 +34,9 @@
  *    zero and the coastal point's coefficients; the recursions run over the
  *    extended segment and only the sea points are read back.  Land output 0.
  *    For K > 1 every iteration re-extends with zeros (imaginary values are not
- *    carried between iterations).
+ *    carried between iterations).  img_factor = +infinity is the infinite
+ *    imaginary sea, realised by an extension long enough that the neglected
+ *    tail is below FP64 resolution (n_imaginary).
  *  - Constant-extension coasts (an option; one of the alternative coast
  *    conditions the Conclusions leave for future work): the imaginary
  *    points carry the value of the adjacent sea point (the first sea point's
@@ -134,10 +136,24 @@ static void ws_free(orc_ws *w)
     memset(w, 0, sizeof(*w));
 }
 
+/* Imaginary points at a coast whose sea point has length scale sigma_coast.
+ * img_factor = +infinity is the infinite imaginary sea: the recursions run on
+ * forever with zero input, and since the filters' poles lie inside the unit
+ * circle (|z| <= 1 - 0.5/(1 + sigma) for both filters; the pins check the
+ * spectral radius) the extension is cut at ceil(60 (1 + 2 sigma_coast))
+ * points, beyond which the neglected part of the response is below e^-100 of
+ * it, far under FP64 resolution. */
 static int64_t n_imaginary(double img_factor, double sigma_coast)
 {
     if (!(img_factor > 0.0)) return 0;
+    if (isinf(img_factor)) return (int64_t)ceil(60.0 * (1.0 + 2.0 * sigma_coast));
     return (int64_t)ceil(img_factor * sigma_coast);
+}
+
+/* Public: the number of imaginary points the oracle uses at a coast. */
+int64_t orc_n_imaginary(double img_factor, double sigma_coast)
+{
+    return n_imaginary(img_factor, sigma_coast);
 }
 
 /* Coefficients of the extended segment: imaginary points take the
@@ -272,6 +288,53 @@ int orc_line(int order, int iters, int adjoint, double img_factor, int norm,
     return rc;
 }
 
+/* One level slice of one variable: V_H (or its adjoint) of src into dst,
+ * with the slice's mask and length scales; tmp is a plane of scratch and
+ * li/lo/ls/lm line buffers of max(nx, ny). */
+static int slice_apply(int order, int iters, int adjoint, double img_factor, int norm,
+                       int qcorr, int coast, int64_t nx, int64_t ny, const uint8_t *mk,
+                       const double *sx, const double *sy, const double *src, double *dst,
+                       double *tmp, double *li, double *lo, double *ls, uint8_t *lm,
+                       orc_ws *w)
+{
+    int rc = ORC_OK;
+    for (int pass = 0; pass < 2 && rc == ORC_OK; ++pass) {
+        /* forward: x then y; adjoint: y then x */
+        int along_x = adjoint ? (pass == 1) : (pass == 0);
+        const double *a = pass == 0 ? src : tmp;
+        double *b = pass == 0 ? tmp : dst;
+        if (along_x) {
+            for (int64_t j = 0; j < ny && rc == ORC_OK; ++j)
+                rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr, coast,
+                                nx, mk + j * nx, sx + j * nx, a + j * nx, b + j * nx, w);
+        } else {
+            for (int64_t i = 0; i < nx && rc == ORC_OK; ++i) {
+                for (int64_t j = 0; j < ny; ++j) {
+                    lm[j] = mk[j * nx + i];
+                    ls[j] = sy[j * nx + i];
+                    li[j] = a[j * nx + i];
+                }
+                rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr, coast,
+                                ny, lm, ls, li, lo, w);
+                for (int64_t j = 0; j < ny; ++j) b[j * nx + i] = lo[j];
+            }
+        }
+    }
+    return rc;
+}
+
+/* Threads of orc_vh's loop over the (variable, level) slices, the paper's
+ * own parallel axis (OpenMP over levels, Sec. 5); 1 by default.  The slices
+ * are independent and each is computed sequentially, so the result does not
+ * depend on the thread count. */
+static int g_threads = 1;
+
+int orc_set_threads(int n)
+{
+    g_threads = n < 1 ? 1 : n;
+    return g_threads;
+}
+
 /* Public: V_H = G_y G_x (or its adjoint G_x^T G_y^T) on fields laid out
  * [nvar][nz][ny][nx], x fastest.  mask is [mask_nz][ny][nx], Lx and Ly are
  * [L_nz][ny][nx] in grid units; mask_nz and L_nz are 1 (shared by every
@@ -285,47 +348,33 @@ int orc_vh(int order, int iters, int adjoint, double img_factor, int norm,
     if (nx < 0 || ny < 0 || nz < 0 || nvar < 0) return ORC_EINVAL;
     if (!(mask_nz == 1 || mask_nz == nz) || !(L_nz == 1 || L_nz == nz))
         return ORC_EINVAL;
-    int64_t plane = nx * ny, nmax = nx > ny ? nx : ny;
-    double *tmp = (double *)malloc(sizeof(double) * (size_t)(plane ? plane : 1));
-    double *li = (double *)malloc(sizeof(double) * (size_t)(nmax ? nmax : 1));
-    double *lo = (double *)malloc(sizeof(double) * (size_t)(nmax ? nmax : 1));
-    double *ls = (double *)malloc(sizeof(double) * (size_t)(nmax ? nmax : 1));
-    uint8_t *lm = (uint8_t *)malloc((size_t)(nmax ? nmax : 1));
-    orc_ws w = {0};
-    int rc = (tmp && li && lo && ls && lm) ? ORC_OK : ORC_ENOMEM;
-    for (int64_t v = 0; v < nvar && rc == ORC_OK; ++v) {
-        for (int64_t k = 0; k < nz && rc == ORC_OK; ++k) {
-            const uint8_t *mk = mask + (mask_nz == 1 ? 0 : k) * plane;
-            const double *sx = Lx + (L_nz == 1 ? 0 : k) * plane;
-            const double *sy = Ly + (L_nz == 1 ? 0 : k) * plane;
-            const double *src = in + (v * nz + k) * plane;
-            double *dst = out + (v * nz + k) * plane;
-            for (int pass = 0; pass < 2 && rc == ORC_OK; ++pass) {
-                /* forward: x then y; adjoint: y then x */
-                int along_x = adjoint ? (pass == 1) : (pass == 0);
-                const double *a = pass == 0 ? src : tmp;
-                double *b = pass == 0 ? tmp : dst;
-                if (along_x) {
-                    for (int64_t j = 0; j < ny && rc == ORC_OK; ++j)
-                        rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr, coast,
-                                        nx, mk + j * nx, sx + j * nx,
-                                        a + j * nx, b + j * nx, &w);
-                } else {
-                    for (int64_t i = 0; i < nx && rc == ORC_OK; ++i) {
-                        for (int64_t j = 0; j < ny; ++j) {
-                            lm[j] = mk[j * nx + i];
-                            ls[j] = sy[j * nx + i];
-                            li[j] = a[j * nx + i];
-                        }
-                        rc = line_apply(order, iters, adjoint, img_factor, norm, qcorr, coast,
-                                        ny, lm, ls, li, lo, &w);
-                        for (int64_t j = 0; j < ny; ++j) b[j * nx + i] = lo[j];
-                    }
-                }
-            }
+    const int64_t plane = nx * ny, nmax = nx > ny ? nx : ny, nslices = nvar * nz;
+    int rc = ORC_OK;
+#pragma omp parallel num_threads(g_threads) if (g_threads > 1)
+    {
+        double *tmp = (double *)malloc(sizeof(double) * (size_t)(plane ? plane : 1));
+        double *li = (double *)malloc(sizeof(double) * (size_t)(nmax ? nmax : 1));
+        double *lo = (double *)malloc(sizeof(double) * (size_t)(nmax ? nmax : 1));
+        double *ls = (double *)malloc(sizeof(double) * (size_t)(nmax ? nmax : 1));
+        uint8_t *lm = (uint8_t *)malloc((size_t)(nmax ? nmax : 1));
+        orc_ws w = {0};
+        int my = (tmp && li && lo && ls && lm) ? ORC_OK : ORC_ENOMEM;
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t s = 0; s < nslices; ++s) {
+            if (my != ORC_OK) continue;
+            const int64_t v = s / nz, k = s % nz;
+            (void)v;
+            my = slice_apply(order, iters, adjoint, img_factor, norm, qcorr, coast, nx, ny,
+                             mask + (mask_nz == 1 ? 0 : k) * plane,
+                             Lx + (L_nz == 1 ? 0 : k) * plane, Ly + (L_nz == 1 ? 0 : k) * plane,
+                             in + s * plane, out + s * plane, tmp, li, lo, ls, lm, &w);
         }
+        if (my != ORC_OK) {
+#pragma omp critical
+            rc = my;
+        }
+        ws_free(&w);
+        free(tmp); free(li); free(lo); free(ls); free(lm);
     }
-    ws_free(&w);
-    free(tmp); free(li); free(lo); free(ls); free(lm);
     return rc;
 }

@@ -119,6 +119,58 @@ __host__ __device__ inline void tail_map_fp64(double sigma, int n_img, int order
     }
 }
 
+// Boundary map of the infinite imaginary sea (img_factor = infinity): the
+// limit of tail_map_fp64 as n -> infinity,
+//   M = sum_{j>=0} A^j Q A^j,  Q = b c^T A,
+// which converges because the filter's poles lie inside the unit circle and
+// is the solution of the Stein equation M = Q + A M A.  Solved directly as
+// the 9 x 9 linear system (I - K) vec(M) = vec(Q), K[(r,q),(s,t)] =
+// A[r][s] A[t][q] (row-major vec), by Gaussian elimination with partial
+// pivoting in FP64.  Order 1: M = b a / (1 - a^2) with a = 1 - e.
+__host__ __device__ inline void tail_map_inf_fp64(double sigma, int order, int K, int norm,
+                                                  bool qc, double *m)
+{
+    Coef64 c = coef_fp64(sigma, order, K, norm, qc);
+    for (int r = 0; r < 9; ++r) m[r] = 0.0;
+    if (order == 1) {
+        const double a = 1.0 - c.e;
+        m[0] = c.beta * a / ((1.0 - a) * (1.0 + a));
+        return;
+    }
+    const double A[9] = {1.0 - c.e, 1.0 - c.c1, 1.0 - c.c2,
+                         -c.e,      1.0 - c.c1, 1.0 - c.c2,
+                         -c.e,      -c.c1,      1.0 - c.c2};
+    double S[9][10];   // [I - K | vec Q]
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) {
+            const int row = 3 * r + q;
+            for (int s = 0; s < 3; ++s)
+                for (int t = 0; t < 3; ++t)
+                    S[row][3 * s + t] = (row == 3 * s + t ? 1.0 : 0.0) - A[3 * r + s] * A[3 * t + q];
+            S[row][9] = c.beta * A[q];   // Q = b c^T A, b = beta (1,1,1), c^T A = row 0 of A
+        }
+    for (int col = 0; col < 9; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 9; ++r)
+            if (fabs(S[r][col]) > fabs(S[piv][col])) piv = r;
+        if (piv != col)
+            for (int k = 0; k < 10; ++k) {
+                const double t = S[col][k];
+                S[col][k] = S[piv][k];
+                S[piv][k] = t;
+            }
+        for (int r = col + 1; r < 9; ++r) {
+            const double f = S[r][col] / S[col][col];
+            for (int k = col; k < 10; ++k) S[r][k] -= f * S[col][k];
+        }
+    }
+    for (int r = 8; r >= 0; --r) {
+        double v = S[r][9];
+        for (int k = r + 1; k < 9; ++k) v -= S[r][k] * m[k];
+        m[r] = v / S[r][r];
+    }
+}
+
 // Vectors of the constant-extension coasts (an option: the imaginary points
 // carry the adjacent sea value instead of zero; one of the other coastal
 // boundary conditions the Conclusions leave for future work).  With A, b, c

@@ -180,12 +180,17 @@ rf_status check_options(const rf_options &o)
 {
     if (o.order != 1 && o.order != 3) return RF_EINVAL;
     if (o.iters < 1 || (o.order == 3 && o.iters != 1)) return RF_EINVAL;
-    if (!(o.img_factor >= 0.0) || !std::isfinite(o.img_factor)) return RF_EINVAL;
+    if (!(o.img_factor >= 0.0)) return RF_EINVAL;   // NaN or negative; +inf is allowed
     if (o.norm != RF_NORM_GAUSS_PEAK && o.norm != RF_NORM_UNIT_SUM) return RF_EINVAL;
     if ((o.flags & ~(RF_FLAG_Q_CORRECTED | RF_FLAG_COAST_CONSTANT)) != 0 || o.chunk < 0 ||
         o.tile < 0)
         return RF_EINVAL;
+    // the kernels derive chunk lengths and tile shapes from the line length
+    // (the autotuner picks launch shapes); no override is built
+    if (o.chunk != 0 || o.tile != 0) return RF_EUNSUPPORTED;
     if ((o.flags & RF_FLAG_Q_CORRECTED) && o.order != 3) return RF_EINVAL;
+    // the infinite imaginary sea is built for zero-input coasts only
+    if (std::isinf(o.img_factor) && (o.flags & RF_FLAG_COAST_CONSTANT)) return RF_EUNSUPPORTED;
     return RF_OK;
 }
 
@@ -267,7 +272,10 @@ __global__ void tail_kernel(int64_t n, const TailSpec *__restrict__ spec,
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double m[9];
-    tail_map_fp64((double)spec[i].sigma, spec[i].n_img, order, K, norm, qc != 0, m);
+    if (spec[i].n_img < 0)
+        tail_map_inf_fp64((double)spec[i].sigma, order, K, norm, qc != 0, m);
+    else
+        tail_map_fp64((double)spec[i].sigma, spec[i].n_img, order, K, norm, qc != 0, m);
     for (int r = 0; r < 9; ++r) {
         const float hi = (float)m[r];
         tmap[9 * i + r] = make_float2(hi, (float)(m[r] - (double)hi));
@@ -485,9 +493,13 @@ __global__ void reg_tables_kernel(int64_t nlines, int64_t n, int C, int P, int o
     }
 }
 
+// Imaginary points at a coast: ceil(img_factor sigma); -1 marks the
+// infinite imaginary sea (img_factor = +inf), whose map is the closed-form
+// limit.
 int n_imaginary(double img_factor, float sigma)
 {
     if (!(img_factor > 0.0)) return 0;
+    if (std::isinf(img_factor)) return -1;
     return (int)std::ceil(img_factor * (double)sigma);
 }
 

@@ -66,13 +66,32 @@ def test_rf_coeffs_rejects_bad_arguments(lib):
             setattr(o, k, v)
         return o
     for o in [with_(order=2), with_(order=3, iters=2), with_(order=1, iters=0),
-              with_(img_factor=-1.0), with_(img_factor=float("inf")),
+              with_(img_factor=-1.0), with_(img_factor=float("-inf")),
               with_(img_factor=float("nan")), with_(norm=5), with_(flags=4),
+              with_(chunk=-1), with_(tile=-3),
               with_(flags=_lib.RF_FLAG_COAST_CONSTANT | 8),
               with_(order=1, iters=5, flags=_lib.RF_FLAG_Q_CORRECTED),
               with_(order=1, iters=5,
                     flags=_lib.RF_FLAG_Q_CORRECTED | _lib.RF_FLAG_COAST_CONSTANT)]:
         assert _coeffs(lib, ok_grid, o) == E
+
+
+def test_rf_coeffs_refuses_what_this_build_does_not_provide(lib):
+    """Valid requests the library does not build return RF_EUNSUPPORTED
+    before any GPU work: chunk-length and tile-shape overrides (the kernels
+    derive both from the line length), and the infinite imaginary sea with
+    constant-extension coasts."""
+    ok_grid = _lib.rf_grid(16, 8, 2, 1, 1)
+    U = _lib.RF_EUNSUPPORTED
+
+    def with_(**kw):
+        o = _lib.rf_options_default()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+    for o in [with_(chunk=32), with_(tile=4), with_(chunk=1, tile=1),
+              with_(img_factor=float("inf"), flags=_lib.RF_FLAG_COAST_CONSTANT)]:
+        assert _coeffs(lib, ok_grid, o) == U
 
 
 def test_apply_rejects_bad_arguments(lib):

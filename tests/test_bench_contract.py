@@ -1,5 +1,5 @@
-"""The benchmark's reference arm (the FP64 oracle timed on the host) runs
-without a GPU: its one JSON line carries the keys of the benchmark contract
+"""The benchmark's reference arm (the FP64 oracle timed on all host cores,
+one whole-field forward + adjoint application per step) runs without a GPU: its one JSON line carries the keys of the benchmark contract
 with the same metric and configuration as the GPU arm, and the GPU arm's
 helpers compute the workload and the algorithmic bytes the roofline uses."""
 import json
@@ -24,7 +24,9 @@ def test_reference_arm_prints_one_contract_line():
     assert KEYS <= set(d)
     assert d["impl"] == "reference" and d["unit"] == "Gpts/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
-    assert d["cpu_baseline"]["cores"] == 1
+    # the oracle runs on every core the process may use (OpenMP over slices)
+    assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+    assert "whole field" in d["cpu_baseline"]["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["nx"] == 1024 and d["config"]["ny"] == 384 and d["config"]["nz"] == 72
     assert d["config"]["nvar"] == 2

@@ -136,6 +136,22 @@ def test_options_img_factor_and_norm(cfg2_small, img, norm):
 
 
 @pytest.mark.parametrize("adjoint", [False, True])
+def test_infinite_imaginary_sea(cfg2_small, adjoint):
+    """img_factor = inf: the plan's closed-form limit map (the Stein equation
+    of the boundary map, FP64) against the oracle's explicit extension cut
+    below FP64 resolution, on the coastal regional grid (length scales up to
+    40), both filters; and the limit is approached by a long finite sea."""
+    w = cfg2_small
+    x = w["x"][:, :1]
+    for order, K in FILTERS:
+        g = run_gpu(w, x, order, K, adjoint, img=float("inf"))
+        o = run_oracle(w, x, order, K, adjoint, img=float("inf"))
+        assert rel_err(g, o) <= TOL
+        far = run_gpu(w, x, order, K, adjoint, img=60.0)
+        assert rel_err(far, g) <= TOL
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
 @pytest.mark.parametrize("img,norm", [(3.0, 0), (0.0, 1)])
 def test_q_corrected_filter(cfg2_small, cfg1, adjoint, img, norm):
     """The q-corrected 3rd-RF (an option, not the paper's filter) against the

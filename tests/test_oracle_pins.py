@@ -310,6 +310,66 @@ def test_imaginary_points_equal_zero_padded_sea():
     np.testing.assert_allclose(y1, G @ x, rtol=1e-12, atol=1e-13)
 
 
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 5)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_infinite_imaginary_sea_equals_long_zero_padding(order, K, adjoint):
+    """img_factor = inf (the infinite imaginary sea) on a segment equals the
+    same segment in the middle of an all-sea line padded on each side with
+    zero input and the coastal length scale, filtered with no imaginary
+    points and read back on the segment.  The padding (2000 points for the
+    3rd-RF, 500 for the 1st-RF: 50 and 12 length scales at sigma <= 40) is
+    long enough for the response to die out.  For K > 1 every iteration
+    re-pads with zeros: K applications of the pair matrix of the K-filter
+    (dense triangular solves) on the padded line."""
+    rng = np.random.default_rng(12)
+    L = 60
+    pad = 2000 if order == 3 else 500
+    sig = rng.uniform(2.0, 40.0, L)
+    x = rng.standard_normal(L)
+    y = orc.line(x, sig, img_factor=np.inf, order=order, iters=K, adjoint=adjoint)
+    pad_sig = np.concatenate([[sig[0]] * pad, sig, [sig[-1]] * pad])
+    if order == 3:
+        pad_x = np.concatenate([np.zeros(pad), x, np.zeros(pad)])
+        ref = orc.line(pad_x, pad_sig, img_factor=0.0, adjoint=adjoint)[pad:pad + L]
+    else:
+        G = dense_pair_matrix(pad_sig, 1, K, 0)
+        if adjoint:
+            G = G.T
+        blk = G[pad:pad + L, pad:pad + L]   # zero padding in, restriction out
+        ref = np.linalg.matrix_power(blk, K) @ x
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 1), (1, 5)])
+def test_infinite_imaginary_sea_cut_is_below_fp64(order, K):
+    """The oracle cuts the infinite imaginary sea at n points; the part it
+    drops decays like rho^n with rho the spectral radius of the one-step
+    companion matrix of the recursion (from the oracle's own coefficients).
+    rho^n must be below 1e-30 over the length scales in use."""
+    for sigma in [0.3, 0.7, 1.5, 3.0, 10.0, 40.0, 200.0]:
+        if order == 3:
+            _, al, _ = orc.rf3_coeffs(sigma)
+            comp = np.array([al, [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+            rho = np.max(np.abs(np.linalg.eigvals(comp)))
+        else:
+            rho, _ = orc.rf1_coeffs(sigma, K)
+        n = orc.n_imaginary(np.inf, sigma)
+        assert rho < 1.0
+        assert n * np.log(rho) < np.log(1e-30), (sigma, rho, n)
+
+
+def test_infinite_imaginary_sea_adjoint_dot_product():
+    rng = np.random.default_rng(13)
+    n = 90
+    mask = (rng.random(n) > 0.25).astype(np.uint8)
+    sig = rng.uniform(1.5, 30.0, n)
+    for order, K in [(3, 1), (1, 5)]:
+        x, y = rng.standard_normal(n), rng.standard_normal(n)
+        a = orc.line(x, sig, mask, order=order, iters=K, img_factor=np.inf)
+        b = orc.line(y, sig, mask, order=order, iters=K, img_factor=np.inf, adjoint=True)
+        assert abs(a @ y - x @ b) <= 1e-12 * np.linalg.norm(a) * np.linalg.norm(y)
+
+
 def test_land_isolates_signal():
     """An impulse on one side of a one-cell land strip gives exactly zero on
     the other side, in 1-D and behind a full land wall in 2-D."""
@@ -592,6 +652,26 @@ def test_gaussian_comparison_trends():
 
 
 # ------------------------------------------------------------- validation
+def test_threads_do_not_change_the_result():
+    """vh() on several threads (OpenMP over the (variable, level) slices)
+    equals the single-thread result bit for bit: every slice is computed
+    sequentially and independently."""
+    rng = np.random.default_rng(14)
+    nx, ny, nz = 37, 23, 5
+    mask = (rng.random((ny, nx)) > 0.3).astype(np.uint8)
+    L = rng.uniform(1.0, 9.0, (ny, nx))
+    x = rng.standard_normal((2, nz, ny, nx))
+    a = orc.vh(x, mask, L, L * 0.7, order=3)
+    try:
+        orc.set_threads(4)
+        b = orc.vh(x, mask, L, L * 0.7, order=3)
+        c = orc.vh(x, mask, L, L * 0.7, order=1, iters=5, adjoint=True)
+    finally:
+        orc.set_threads(1)
+    assert np.array_equal(a, b)
+    assert np.array_equal(c, orc.vh(x, mask, L, L * 0.7, order=1, iters=5, adjoint=True))
+
+
 def test_invalid_inputs_rejected():
     with pytest.raises(ValueError):
         orc.line(np.ones(5), -1.0)
