@@ -493,6 +493,61 @@ def test_remark1_valid_bounds(order, K):
     assert np.linalg.norm(err) <= np.abs(eps_h).sum() * np.linalg.norm(s0)
 
 
+def dense_gaussian(mask, sigma):
+    """Brute force: G_ij = exp(-|r_i - r_j|^2 / (2 sigma^2)) between the grid
+    points of a [ny][nx] grid (row-major), zero rows and columns at land."""
+    ny, nx = mask.shape
+    jj, ii = np.divmod(np.arange(ny * nx), nx)
+    r2 = (jj[:, None] - jj[None, :]) ** 2 + (ii[:, None] - ii[None, :]) ** 2
+    G = np.exp(-r2 / (2.0 * sigma * sigma))
+    sea = mask.ravel().astype(bool)
+    G[~sea, :] = 0.0
+    G[:, ~sea] = 0.0
+    return G
+
+
+@pytest.mark.parametrize("order,K", [(3, 1), (1, 5)])
+def test_dense_gaussian_brute_force_2d(order, K):
+    """V_H against the dense 2-D Gaussian matrix-vector product G x on a
+    24 x 32 grid at sigma = 3.  All sea with the infinite imaginary sea,
+    V_H is the restriction of the 2-D convolution with h_x (x) h_y (h the
+    1-D impulse response), so the two valid forms of Remark 1 hold in 2-D
+    with eps_h = g - h_x (x) h_y: pointwise |V x - G x| <= ||eps_h||_2 ||x||_2
+    and ||V x - G x||_2 <= ||eps_h||_1 ||x||_2.  With land (25 % scattered
+    land points) the Gaussian reaches across land and the filters do not;
+    land rows stay exactly zero.  The relative distances ||V x - G x|| /
+    ||G x|| are the reported comparison (about 0.37 for the 3rd-RF and 0.15
+    for the 1st-RF x5 all sea, about 0.66 for both with land)."""
+    rng = np.random.default_rng(15)
+    ny, nx, sigma = 24, 32, 3.0
+    L = np.full((ny, nx), sigma)
+    # all sea, infinite imaginary sea: the bounds
+    mask = np.ones((ny, nx), np.uint8)
+    x = rng.standard_normal((ny, nx))
+    v = orc.vh(x, mask, L, L, order=order, iters=K, img_factor=np.inf)
+    gx = (dense_gaussian(mask, sigma) @ x.ravel()).reshape(ny, nx)
+    n = 401
+    imp = np.zeros(n)
+    imp[n // 2] = 1.0
+    h = orc.line(imp, sigma, order=order, iters=K, img_factor=np.inf)
+    d = np.arange(n) - n // 2
+    eps = np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / (2 * sigma * sigma)) - np.outer(h, h)
+    err = v - gx
+    xn = np.linalg.norm(x)
+    assert np.abs(err).max() <= np.linalg.norm(eps) * xn
+    assert np.linalg.norm(err) <= np.abs(eps).sum() * xn
+    rel_sea = np.linalg.norm(err) / np.linalg.norm(gx)
+    assert (0.25 < rel_sea < 0.5) if order == 3 else (0.08 < rel_sea < 0.25)
+    # with land: the brute-force comparison, land exactly zero
+    mask = (rng.random((ny, nx)) > 0.25).astype(np.uint8)
+    x = rng.standard_normal((ny, nx)) * mask
+    v = orc.vh(x, mask, L, L, order=order, iters=K, img_factor=3.0)
+    gx = (dense_gaussian(mask, sigma) @ x.ravel()).reshape(ny, nx)
+    assert np.all(v[mask == 0] == 0.0)
+    rel_land = np.linalg.norm(v - gx) / np.linalg.norm(gx)
+    assert rel_sea < rel_land < 1.0
+
+
 # ------------------------------------------- constant-extension coasts
 def dense_const_line_matrix(mask, sig, order=3, K=1, img=3.0, norm=0):
     """The line operator with constant-extension coasts as a dense matrix:
