@@ -12,8 +12,11 @@ for T and S) is larger than the 126 MB L2, so no L2 flush is needed.
 `--levels N` runs the first N levels only (a smaller case for profiling).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--levels N]
+                       [--shard]
 Under torchrun each rank runs its own batch (weak scaling, no data-path
-collective); rank 0 prints one JSON line.
+collective); rank 0 prints one JSON line.  With --shard the ranks split the
+one field's levels instead (shard.partition; strong scaling, each rank a Plan
+over its own level range, still no collective on the data path).
 """
 from __future__ import annotations
 
@@ -50,6 +53,8 @@ def parse():
                    help="skip the 64-domain ragged batch and the other configurations")
     p.add_argument("--levels", type=int, default=None,
                    help="use only the first N of the 72 levels (a smaller case for profiling)")
+    p.add_argument("--shard", action="store_true",
+                   help="split the levels of the one field across the ranks (strong scaling)")
     return p.parse_args()
 
 
@@ -633,6 +638,99 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def run_shard(args):
+    """Strong scaling of the level-sharded operator: the world's ranks split
+    the regional field's 72 levels (shard.partition), each rank builds and
+    tunes a Plan over its own levels and times fwd + adjoint steps on them;
+    value = all points of the field / the slowest rank's step time."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1404_5756_gb300 import Options, shard
+
+    w = make_inputs(args.levels)
+    nvar, nz, ny, nx = w["x"].shape
+    npts = nvar * nz * ny * nx
+    doms = [dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=nz)]
+    op = shard.RankOperator(doms, rank, world, Options(order=3), device=dev)
+    mine = sum(nvar * p.nk * ny * nx for p in op.pieces)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    ms_step, launches, clocks = 0.0, 0, None
+    if op.plan is not None:
+        if len(op.pieces) == 1:
+            op.plan.tune(nvar)
+        else:
+            op.plan.tune_batch(nvar)
+        x = op.parts([w["x"]])
+        y = [torch.empty_like(t) for t in x]
+        z = [torch.empty_like(t) for t in x]
+    barrier()
+    with ClockSampler(local) as clk:
+        if op.plan is not None:
+            total_ms, _, _, launches = timed_loop(torch, op.plan, x, y, z, args.steps,
+                                                  args.warmup, stream, "rf3_shard_timed")
+            ms_step = total_ms / args.steps
+    barrier()
+    clocks = clk.summary()
+    ms_step = max_over_ranks(torch, world, ms_step)
+    # end to end on this rank's pinned host buffers
+    e2e_val = None
+    if op.plan is not None:
+        xh = [t.cpu().pin_memory() for t in x]
+        yh = [torch.empty_like(t).pin_memory() for t in xh]
+        zh = [torch.empty_like(t).pin_memory() for t in xh]
+        op.plan.apply_host(xh, yh, nvar=nvar)
+        op.plan.apply_host(yh, zh, nvar=nvar, adjoint=True)
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    if op.plan is not None:
+        for _ in range(e2e_steps):
+            op.plan.apply_host(xh, yh, nvar=nvar)
+            op.plan.apply_host(yh, zh, nvar=nvar, adjoint=True)
+    e2e_s = max_over_ranks(torch, world, time.perf_counter() - t0)
+    e2e_val = 2 * npts * e2e_steps / e2e_s / 1e9
+    op.close()
+    if rank == 0:
+        peak, peak_kind = hbm_peak()
+        alg = algorithmic_bytes(nx, ny, nz, nvar)
+        achieved = alg / (ms_step / 2 * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": 2 * npts / (ms_step * 1e-3) / 1e9, "unit": "Gpts/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(nz), "nx": nx, "ny": ny, "nz": nz,
+                       "nvar": nvar, "points_per_step": 2 * npts,
+                       "l2": f"inputs larger than L2 ({4 * npts / 1e6:.0f} MB field)",
+                       "parallelism": f"levels split over {world} ranks (shard.partition)",
+                       "rank0_points": mine},
+            "clocks": clocks,
+            "e2e": {"value": e2e_val, "unit": "Gpts/s",
+                    "h2d_bytes_per_step": 2 * 4 * npts, "d2h_bytes_per_step": 2 * 4 * npts},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak * world,
+                         "unit": "GB/s", "frac": achieved / (peak * world),
+                         "peak_kind": f"{peak_kind} (copy bandwidth) x {world} GPUs",
+                         "traffic": None},
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def bind_to_gpu_numa_node(torch, dev):
     """Run on the CPUs next to the GPU, so the pinned host buffers of the
     end-to-end measurement are placed on its NUMA node (first touch) rather
@@ -670,6 +768,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.shard:
+        run_shard(args)
     else:
         run_gpu(args)
 

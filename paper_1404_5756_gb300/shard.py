@@ -6,7 +6,7 @@ levels in parallel with OpenMP for the same reason, Section 4).  A rank can
 therefore take any set of slices and filter them with no exchange at all.
 This module decides which levels of which domains a rank owns and cuts the
 plan inputs and fields to match; the rank then builds an ordinary plan for
-its sub-domains.  No collective sits on the data path.
+its sub-domains (RankOperator).  No collective sits on the data path.
 
 Units are (domain, level) pairs, weighted by their horizontal points; the
 pairs are laid out domain after domain, level after level, and cut into
@@ -111,3 +111,41 @@ def assemble(domains, nvar: int, gathered: list[list[tuple[Piece, np.ndarray]]])
                 out[p.domain] = np.zeros((nvar, nz) + tuple(y.shape[2:]), y.dtype)
             out[p.domain][:, p.k0:p.k0 + p.nk] = y
     return out
+
+
+class RankOperator:
+    """V_H on the pieces one rank owns: one Plan (on this process's GPU) over
+    the rank's sub-domains, a ragged batch of level ranges, applied in one
+    call with no exchange between ranks.  `parts` cuts the rank's inputs out
+    of the full fields (host arrays or tensors, one [nvar][nz][ny][nx] per
+    domain) onto the device; `apply` filters them and returns
+    [(piece, output)] for `assemble`."""
+
+    def __init__(self, domains, rank: int, world: int, options=None, device="cuda"):
+        from .vh import Plan
+        self.pieces = partition(domains, world)[rank]
+        self.plan = None
+        if self.pieces:
+            subs = [sub_domain(domains[p.domain], p.k0, p.nk) for p in self.pieces]
+            self.plan = Plan(subs, options, device=device)
+
+    def parts(self, fields):
+        """The rank's input parts on the plan's device (float32, contiguous)."""
+        import torch
+        out = []
+        for p in self.pieces:
+            x = take(fields[p.domain], p.k0, p.nk)
+            x = x if torch.is_tensor(x) else torch.from_numpy(np.ascontiguousarray(x, np.float32))
+            out.append(x.to(self.plan.device, torch.float32).contiguous())
+        return out
+
+    def apply(self, parts, outs=None, adjoint: bool = False):
+        if not self.pieces:
+            return []
+        ys = self.plan._run(list(parts), None if outs is None else list(outs), adjoint)
+        return list(zip(self.pieces, ys))
+
+    def close(self):
+        if self.plan is not None:
+            self.plan.close()
+            self.plan = None
