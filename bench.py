@@ -367,7 +367,7 @@ def run_configs(torch, dev, steps, warmup, peak):
     roofline).  global_1440x1080x75: one variable on the global grid (30 %
     land, L from 30 at the equator to 4 at the poles), forward + adjoint per
     step after tuning, with its own roofline fraction."""
-    from paper_1404_5756_gb300 import Plan, synth
+    from paper_1404_5756_gb300 import Options, Plan, synth
     stream = torch.cuda.current_stream(dev)
     out = {}
     w = synth.workload(1, fields=False)
@@ -392,30 +392,39 @@ def run_configs(torch, dev, steps, warmup, peak):
                               "value": x.numel() / (us * 1e-6) / 1e9, "unit": "Gpts/s",
                               "note": "one level, 32768 points: launch-latency bound"}
     w = synth.workload(3)
-    plan = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=w["nz"]), device=dev)
-    plan.tune(w["nvar"])
     x = torch.from_numpy(w["x"]).to(dev)
     y, z = torch.empty_like(x), torch.empty_like(x)
-    for _ in range(warmup):
-        plan.apply(x, out=y)
-        plan.apply_adjoint(y, out=z)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        plan.apply(x, out=y)
-        plan.apply_adjoint(y, out=z)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / steps
     npts = x.numel()
     alg = algorithmic_bytes(w["nx"], w["ny"], w["nz"], w["nvar"])
+
+    def timed_global(options):
+        plan = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=w["nz"]), options, device=dev)
+        plan.tune(w["nvar"])
+        for _ in range(warmup):
+            plan.apply(x, out=y)
+            plan.apply_adjoint(y, out=z)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.apply(x, out=y)
+            plan.apply_adjoint(y, out=z)
+        e1.record(stream)
+        e1.synchronize()
+        plan.close()
+        return e0.elapsed_time(e1) / steps
+
+    ms = timed_global(Options(order=3))
+    ms1 = timed_global(Options(order=1, iters=5))
     achieved = alg / (ms / 2 * 1e-3) / 1e9
     out["global_1440x1080x75"] = {"value": 2 * npts / (ms * 1e-3) / 1e9, "unit": "Gpts/s",
                                   "ms_per_step": ms, "points": npts,
                                   "roofline": {"bound": "hbm", "achieved": achieved,
                                                "peak": peak, "unit": "GB/s",
-                                               "frac": achieved / peak}}
+                                               "frac": achieved / peak},
+                                  "rf1x5": {"value": 2 * npts / (ms1 * 1e-3) / 1e9,
+                                            "unit": "Gpts/s", "ms_per_step": ms1},
+                                  "speedup_rf3_over_rf1x5": ms1 / ms}
     return out
 
 
