@@ -26,6 +26,7 @@ NORM_GAUSS_PEAK = 0
 NORM_UNIT_SUM = 1
 COAST_ZERO = 0        # imaginary sea points carry zero (the paper's reading)
 COAST_CONSTANT = 1    # imaginary sea points carry the adjacent sea value
+COAST_CARRIED = 2     # imaginary sea points keep their values across 1st-RF iterations
 
 
 def build(force: bool = False) -> str:
@@ -116,7 +117,9 @@ def line(x, sigma, mask=None, *, order: int = 3, iters: int = 1,
          norm: int = NORM_GAUSS_PEAK, qcorr: bool = False,
          coast: int = COAST_ZERO) -> np.ndarray:
     """Apply one 1-D filter G (or G^T) to the line x.  coast: COAST_ZERO
-    (imaginary points carry zero) or COAST_CONSTANT (the adjacent sea value)."""
+    (imaginary points carry zero), COAST_CONSTANT (the adjacent sea value) or
+    COAST_CARRIED (zero at first, then their own values from iteration to
+    iteration)."""
     lib = _load()
     x = np.ascontiguousarray(x, dtype=np.float64)
     n = x.shape[0]

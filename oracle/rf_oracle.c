@@ -34,7 +34,7 @@
  *    zero and the coastal point's coefficients; the recursions run over the
  *    extended segment and only the sea points are read back.  Land output 0.
  *    For K > 1 every iteration re-extends with zeros (imaginary values are not
- *    carried between iterations).  img_factor = +infinity is the infinite
+ *    carried between iterations; carried coasts below are the option).  img_factor = +infinity is the infinite
  *    imaginary sea, realised by an extension long enough that the neglected
  *    tail is below FP64 resolution (n_imaginary).
  *  - Constant-extension coasts (an option; one of the alternative coast
@@ -44,6 +44,13 @@
  *    extension E_c is then no longer a zero padding, and its transpose adds
  *    the adjoint's values at the imaginary points to the edge point they
  *    copied.
+ *  - Carried coasts (an option; another of those alternative conditions):
+ *    for the 1st-RF with K > 1 iterations the segment is extended once with
+ *    zero-input imaginary points and all K iterations run over the extended
+ *    segment, so the values the imaginary points take in one iteration feed
+ *    the next; only the final result is read back: R G_ext^K R^T instead of
+ *    (R G_ext R^T)^K.  The adjoint is R (G_ext^T)^K R^T.  With K = 1 (and for
+ *    the 3rd-RF) it is the zero-input coast.
  *  - The 2-D operator V_H = G_y G_x (Sec. 2.2): rows (x) first, then columns
  *    (y), on every level of every variable.
  *  - The adjoint V_H^T = G_x^T G_y^T, written out as the transposed
@@ -219,7 +226,8 @@ static void forward_backward_adjoint(int64_t m, const double *alpha,
 }
 
 /* One line of n points.  mask[i] != 0 marks sea.  sig[i] = R_i/dx_i.
- * coast: 0 imaginary points carry zero, 1 they carry the adjacent sea value. */
+ * coast: 0 imaginary points carry zero, 1 they carry the adjacent sea value,
+ * 2 they start at zero and keep their values from iteration to iteration. */
 static int line_apply(int order, int iters, int adjoint, double img_factor,
                       int norm, int qcorr, int coast, int64_t n, const uint8_t *mask,
                       const double *sig, const double *in, double *out,
@@ -241,9 +249,12 @@ static int line_apply(int order, int iters, int adjoint, double img_factor,
         for (int64_t t = 0; t < L; ++t) out[b + t] = in[b + t];
         for (int k = 0; k < iters; ++k) {
             /* extend (E, or R^T for the adjoint): zeros, or for the forward
-             * constant extension the edge values */
-            for (int64_t r = 0; r < m; ++r) w->x[r] = 0.0;
-            for (int64_t t = 0; t < L; ++t) w->x[nl + t] = out[b + t];
+             * constant extension the edge values; carried coasts extend
+             * before the first iteration only */
+            if (coast != 2 || k == 0) {
+                for (int64_t r = 0; r < m; ++r) w->x[r] = 0.0;
+                for (int64_t t = 0; t < L; ++t) w->x[nl + t] = out[b + t];
+            }
             if (coast == 1 && !adjoint) {
                 for (int64_t r = 0; r < nl; ++r) w->x[r] = out[b];
                 for (int64_t r = nl + L; r < m; ++r) w->x[r] = out[b + L - 1];
@@ -254,7 +265,8 @@ static int line_apply(int order, int iters, int adjoint, double img_factor,
                 forward_backward(m, w->alpha, w->beta, w->x, w->y);
             /* restrict to the sea points (R, or E^T for the adjoint: with
              * constant extension the imaginary values go to the edge point
-             * they copied) */
+             * they copied); carried coasts keep the extended segment */
+            if (coast == 2 && k < iters - 1) continue;
             for (int64_t t = 0; t < L; ++t) out[b + t] = w->x[nl + t];
             if (coast == 1 && adjoint) {
                 for (int64_t r = 0; r < nl; ++r) out[b] += w->x[r];
@@ -268,7 +280,7 @@ static int line_apply(int order, int iters, int adjoint, double img_factor,
 static int check_opts(int order, int iters, int qcorr, int coast)
 {
     if (order != 1 && order != 3) return ORC_EINVAL;
-    if (coast != 0 && coast != 1) return ORC_EINVAL;
+    if (coast < 0 || coast > 2) return ORC_EINVAL;
     if (qcorr && order != 3) return ORC_EINVAL;
     if (iters < 1) return ORC_EINVAL;
     if (order == 3 && iters != 1) return ORC_EINVAL;

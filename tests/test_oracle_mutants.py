@@ -66,6 +66,10 @@ MUTANTS = {
          "int64_t src = r < nl ? L - 1 : (r >= nl + L ? L - 1 : r - nl);"),
     "adjoint forgets the inner beta":
         ("for (int64_t r = 0; r < m; ++r) z[r] *= beta[r];", "(void)0;"),
+    "carried coasts re-extend with zeros every iteration":
+        ("if (coast != 2 || k == 0) {", "if (1) {"),
+    "carried coasts in the forward operator only":
+        ("if (coast != 2 || k == 0) {", "if (coast != 2 || k == 0 || adjoint) {"),
 }
 
 

@@ -676,6 +676,99 @@ def test_constant_coast_adjoint_dot_product(order, K):
 
 
 # ------------------------------------- comparison with the exact Gaussian
+# ------------------------------------------------- carried coasts
+def dense_carried_line_matrix(mask, sig, K, img, norm=0):
+    """The 1st-RF x K line operator with carried coasts as a dense matrix: per
+    sea run, zero-extend once by ceil(img*sigma) imaginary points with the
+    coastal sigma, apply the pair matrix K times on the extended run, read the
+    sea points back: R G_ext^K R^T."""
+    n = len(mask)
+    G = np.zeros((n, n))
+    i = 0
+    while i < n:
+        if not mask[i]:
+            i += 1
+            continue
+        b = i
+        while i < n and mask[i]:
+            i += 1
+        seg = list(range(b, i))
+        L = len(seg)
+        nl = int(np.ceil(img * sig[b])) if img > 0 else 0
+        nr = int(np.ceil(img * sig[i - 1])) if img > 0 else 0
+        ext = [sig[b]] * nl + [sig[t] for t in seg] + [sig[i - 1]] * nr
+        R = np.zeros((L, len(ext)))
+        R[np.arange(L), nl + np.arange(L)] = 1.0
+        G[np.ix_(seg, seg)] = R @ np.linalg.matrix_power(dense_pair_matrix(ext, 1, K, norm), K) @ R.T
+    return G
+
+
+@pytest.mark.parametrize("K,img", [(2, 1.0), (5, 1.0), (5, 2.5), (3, 0.6)])
+def test_carried_coast_matches_dense_extension_power(K, img):
+    """Carried coasts against their definition as matrices, forward and
+    adjoint (the transpose), on runs that include a one-point segment."""
+    rng = np.random.default_rng(23)
+    n = 26
+    mask = np.ones(n, np.uint8)
+    mask[[0, 5, 6, 8, 17]] = 0           # point 7 is a one-point segment
+    sig = rng.uniform(0.6, 3.0, n)
+    G = dense_carried_line_matrix(mask, sig, K, img)
+    kw = dict(order=1, iters=K, img_factor=img, coast=orc.COAST_CARRIED)
+    O = oracle_line_matrix(mask, sig, **kw)
+    np.testing.assert_allclose(O, G, rtol=0, atol=1e-12 * np.abs(G).max())
+    OT = oracle_line_matrix(mask, sig, adjoint=True, **kw)
+    np.testing.assert_allclose(OT, G.T, rtol=0, atol=1e-12 * np.abs(G).max())
+    # it is a different operator from re-extending with zeros every iteration
+    assert np.abs(dense_line_matrix(mask, sig, 1, K, img) - G).max() > 1e-4
+
+
+def test_carried_coast_equals_iterating_on_the_zero_padded_line():
+    """On one sea run the carried coast is the filter iterated K times on the
+    run padded with explicit sea points carrying the coastal sigma and zero
+    input (no imaginary points: img_factor 0), read back on the run."""
+    rng = np.random.default_rng(31)
+    L, K, img = 40, 5, 2.0
+    sig = rng.uniform(1.0, 4.0, L)
+    x = rng.standard_normal(L)
+    nl, nr = int(np.ceil(img * sig[0])), int(np.ceil(img * sig[-1]))
+    pad_sig = np.concatenate([np.full(nl, sig[0]), sig, np.full(nr, sig[-1])])
+    pad_x = np.concatenate([np.zeros(nl), x, np.zeros(nr)])
+    for adjoint in (False, True):
+        ref = orc.line(pad_x, pad_sig, order=1, iters=K, img_factor=0.0, adjoint=adjoint)[nl:nl + L]
+        got = orc.line(x, sig, order=1, iters=K, img_factor=img, adjoint=adjoint,
+                       coast=orc.COAST_CARRIED)
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_carried_coast_reduces_to_zero_coast_for_one_iteration():
+    rng = np.random.default_rng(37)
+    ny, nx = 14, 19
+    mask = (rng.random((ny, nx)) > 0.3).astype(np.uint8)
+    L = rng.uniform(0.8, 3.0, (ny, nx))
+    x = rng.standard_normal((1, 1, ny, nx))
+    for order in (1, 3):
+        for adjoint in (False, True):
+            a = orc.vh(x, mask, L, L, order=order, iters=1, img_factor=2.0, adjoint=adjoint)
+            b = orc.vh(x, mask, L, L, order=order, iters=1, img_factor=2.0, adjoint=adjoint,
+                       coast=orc.COAST_CARRIED)
+            assert np.array_equal(a, b)
+
+
+def test_carried_coast_adjoint_dot_product_2d():
+    rng = np.random.default_rng(41)
+    ny, nx = 17, 23
+    mask = (rng.random((ny, nx)) > 0.25).astype(np.uint8)
+    Lx = rng.uniform(0.8, 3.5, (ny, nx))
+    Ly = rng.uniform(0.8, 3.5, (ny, nx))
+    x = rng.standard_normal((2, 2, ny, nx))
+    y = rng.standard_normal((2, 2, ny, nx))
+    kw = dict(order=1, iters=5, img_factor=2.5, coast=orc.COAST_CARRIED)
+    vx = orc.vh(x, mask, Lx, Ly, **kw)
+    vty = orc.vh(y, mask, Lx, Ly, adjoint=True, **kw)
+    lhs, rhs = float((vx * y).sum()), float((x * vty).sum())
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
 def test_gaussian_comparison_trends():
     """The filters approximate exp(-r^2 / 2 sigma^2) (reported, not a parity
     bar).  What the mathematics fixes: iterating the first-order pair K times
@@ -737,7 +830,7 @@ def test_invalid_inputs_rejected():
     with pytest.raises(ValueError):
         orc.line(np.ones(5), 2.0, order=1, iters=5, qcorr=True)
     with pytest.raises(ValueError):
-        orc.line(np.ones(5), 2.0, coast=2)
+        orc.line(np.ones(5), 2.0, coast=3)
     # land points may carry any length scale
     mask = np.array([1, 0, 1, 1, 0], np.uint8)
     sig = np.array([2.0, -5.0, 2.0, 3.0, np.nan])
