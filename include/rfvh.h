@@ -73,9 +73,17 @@ enum {
  * zero -- one of the other coastal boundary conditions the Conclusions leave
  * for future work.  The adjoint is the exact transpose: the adjoint values
  * at the imaginary points are added to the edge point they copied.  With
- * img_factor = 0 (no imaginary points) it changes nothing.  Flags combine
- * with |. */
-enum { RF_FLAG_Q_CORRECTED = 1, RF_FLAG_COAST_CONSTANT = 2 };
+ * img_factor = 0 (no imaginary points) it changes nothing.
+ *
+ * RF_FLAG_COAST_CARRIED (not the paper's coasts; another of the conditions
+ * the Conclusions leave open): for the 1st-RF with K > 1 iterations the
+ * imaginary points start at zero and keep, from one iteration to the next,
+ * the values the filter left in them, i.e. each line segment is extended
+ * once, filtered K times and read back once (R G_ext^K R^T instead of
+ * (R G_ext R^T)^K); the adjoint is R (G_ext^T)^K R^T.  For K = 1, the 3rd-RF
+ * or img_factor = 0 it changes nothing.  It excludes RF_FLAG_COAST_CONSTANT
+ * (RF_EINVAL).  Flags combine with |. */
+enum { RF_FLAG_Q_CORRECTED = 1, RF_FLAG_COAST_CONSTANT = 2, RF_FLAG_COAST_CARRIED = 4 };
 
 typedef struct rf_plan_ *rf_plan;
 typedef struct rf_graph_ *rf_graph;
@@ -98,7 +106,8 @@ typedef struct {
                              RF_EUNSUPPORTED); must be >= 0, not NaN          */
     int norm;             /* RF_NORM_GAUSS_PEAK or RF_NORM_UNIT_SUM          */
     int flags;            /* RF_FLAG_Q_CORRECTED (order 3 only) |
-                             RF_FLAG_COAST_CONSTANT, or 0                    */
+                             RF_FLAG_COAST_CONSTANT or RF_FLAG_COAST_CARRIED,
+                             or 0                                            */
     int chunk;            /* chunk-length override: must be 0 (automatic);
                              any other value gives RF_EUNSUPPORTED, since the
                              kernels derive the chunking from the line length */

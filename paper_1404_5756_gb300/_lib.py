@@ -18,6 +18,7 @@ RF_OK, RF_EINVAL, RF_ENOMEM, RF_ECUDA, RF_ETIMEOUT, RF_EUNSUPPORTED = range(6)
 RF_NORM_GAUSS_PEAK, RF_NORM_UNIT_SUM = 0, 1
 RF_FLAG_Q_CORRECTED = 1
 RF_FLAG_COAST_CONSTANT = 2
+RF_FLAG_COAST_CARRIED = 4
 
 
 class rf_grid(ctypes.Structure):

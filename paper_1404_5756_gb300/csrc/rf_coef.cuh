@@ -171,6 +171,106 @@ __host__ __device__ inline void tail_map_inf_fp64(double sigma, int order, int K
     }
 }
 
+// History weights of the carried coasts (an option, 1st-RF with K > 1
+// iterations): the imaginary points of a segment start at zero and keep the
+// values each iteration leaves in them, so after iteration k they hold a
+// linear function of the boundary states the sea saw in iterations 1..k.
+// With a = 1 - e and beta the coastal point's coefficients:
+//   right end (n points after the last sea point): X is the state the first
+//     sweep leaves at the last sea point, u the points' content; one iteration
+//     maps (X, u) to the second sweep's start state Y and the new content u';
+//   left end (n points before the first sea point): v the content; the first
+//     sweep enters the sea with state H(v); S is the state the second sweep
+//     leaves at the first sea point; one iteration maps (S, v) to v'.
+// Forward (G = anticausal o causal, both stepping p = a p + beta x):
+//   right: p = X, p_t = a p_{t-1} + beta u_t (t = 1..n); y_{n+1} = 0,
+//          y_t = a y_{t+1} + beta p_t; Y = y_1, u' = y;
+//   left:  p_{n+1} = 0, p_t = a p_{t+1} + beta v_t (t = n..1, t = 1 next to
+//          the sea); H = p_1; y_0 = S, y_t = a y_{t-1} + beta p_t; v' = y.
+// Adjoint (G^T: the transposed steps l = l + x, out = beta l, l = a l, first
+// left to right, then right to left):
+//   right: l = X; for t = 1..n: l += u_t, w_t = beta l, l = a l; m = 0; for
+//          t = n..1: m += w_t, u'_t = beta m, m = a m; Y = m;
+//   left:  l = 0; for t = n..1: l += v_t, w_t = beta l, l = a l; H = l;
+//          m = S; for t = 1..n: m += w_t, v'_t = beta m, m = a m.
+// By linearity, in iteration k (1-based) the start state injected at the
+// segment's end is Y_k = M X_k + sum_{d=1..k-1} mu_d X_{k-d} and the state
+// entering its first point is H_k = sum_{d=1..k-1} lambda_d S_{k-d}, with
+//   mu_d = Y(0, psi_d), psi_1 = u'(1, 0), psi_{d+1} = u'(0, psi_d);
+//   lambda_d = H(chi_d), chi_1 = v'(1, 0), chi_{d+1} = v'(0, chi_d).
+// carry_weights_fp64 writes mu_1..mu_{K-1} or lambda_1..lambda_{K-1} of one
+// end (n imaginary points at length scale sigma) into w, using buf (2n
+// doubles) as scratch.
+__host__ __device__ inline void carry_weights_fp64(double sigma, int64_t n, int K, int norm,
+                                                   bool adjoint, bool right, double *buf,
+                                                   double *w)
+{
+    const Coef64 c = coef_fp64(sigma, 1, K, norm);
+    const double a = 1.0 - c.e, b = c.beta;
+    double *z = buf, *t = buf + n;   // content, scratch
+    // one iteration of the run with boundary state bs and content z (in
+    // place -> z'); returns Y (right) or H (left, of the incoming content)
+    auto step = [&](double bs) -> double {
+        double out = 0.0;
+        if (!adjoint) {
+            if (right) {
+                double p = bs;
+                for (int64_t i = 0; i < n; ++i) t[i] = p = a * p + b * z[i];
+                double y = 0.0;
+                for (int64_t i = n - 1; i >= 0; --i) z[i] = y = a * y + b * t[i];
+                out = n > 0 ? z[0] : 0.0;
+            } else {
+                double p = 0.0;
+                for (int64_t i = n - 1; i >= 0; --i) t[i] = p = a * p + b * z[i];
+                out = n > 0 ? t[0] : 0.0;
+                double y = bs;
+                for (int64_t i = 0; i < n; ++i) z[i] = y = a * y + b * t[i];
+            }
+        } else {
+            if (right) {
+                double l = bs;
+                for (int64_t i = 0; i < n; ++i) {
+                    l += z[i];
+                    t[i] = b * l;
+                    l *= a;
+                }
+                double m = 0.0;
+                for (int64_t i = n - 1; i >= 0; --i) {
+                    m += t[i];
+                    z[i] = b * m;
+                    m *= a;
+                }
+                out = m;
+            } else {
+                double l = 0.0;
+                for (int64_t i = n - 1; i >= 0; --i) {
+                    l += z[i];
+                    t[i] = b * l;
+                    l *= a;
+                }
+                out = l;
+                double m = bs;
+                for (int64_t i = 0; i < n; ++i) {
+                    m += t[i];
+                    z[i] = b * m;
+                    m *= a;
+                }
+            }
+        }
+        return out;
+    };
+    for (int64_t i = 0; i < n; ++i) z[i] = 0.0;
+    step(1.0);   // z = psi_1 (chi_1)
+    for (int d = 1; d < K; ++d) {
+        if (right) {
+            w[d - 1] = step(0.0);   // Y(0, psi_d), z -> psi_{d+1}
+        } else {
+            // H(chi_d) is the incoming content's entering state; then chi_{d+1}
+            w[d - 1] = step(0.0);
+        }
+    }
+}
+
 // Vectors of the constant-extension coasts (an option: the imaginary points
 // carry the adjacent sea value instead of zero; one of the other coastal
 // boundary conditions the Conclusions leave for future work).  With A, b, c

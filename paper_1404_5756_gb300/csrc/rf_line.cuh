@@ -7,7 +7,11 @@
 // constant-extension coasts (cvec non-null) the causal state entering a
 // segment starts from x_a s and the backward start state gains x_e m
 // (forward); the adjoint adds s.costate and m.lambda to the outputs at the
-// segment's first and last points (see rf_tile.cuh).
+// segment's first and last points (see rf_tile.cuh).  With carried coasts
+// (carry non-null, 1st-RF, K iterations) a segment's record also keeps the
+// state entering it and the boundary states of every iteration: iteration
+// k starts the segment from sum_d lambda_d S_{k-d} and its backward sweep
+// from M X_k + sum_d mu_d X_{k-d} (rf_coef.cuh, carry_weights_fp64).
 #pragma once
 #include <cstdint>
 
@@ -23,7 +27,9 @@ struct LineArgs {
     const float2 *tmap;       // [ntail][9] hi/lo pairs
     const float4 *cvec;       // [ntail][2] (m, s) of constant-extension coasts, or null
     float *tscr;              // [nvar*nz][ntail][nr]
-    int nr;                   // floats per record: 3, or 4 with cvec
+    int nr;                   // floats per record: 3, 4 with cvec, 2 + 2 kc with carry
+    const float *carry;       // [ntail][2][kc - 1] (mu, lambda) of this direction, or null
+    int kc;                   // K of the carried coasts
     int64_t n, nlines, pt_stride, line_stride, plane, ntail, ncl;
     int64_t nz, nvar;         // levels and variables of the field
     int64_t k0, nk;           // this launch filters levels k0 .. k0+nk-1
@@ -47,6 +53,11 @@ __global__ void __launch_bounds__(128) line_kernel(LineArgs a)
     const int64_t n = a.n, ps = a.pt_stride;
     const bool cst = a.cvec != nullptr && a.ntail > 0;
     const float4 *cv = cst ? a.cvec + 2 * base : nullptr;   // this line's segments
+    const bool car = a.carry != nullptr && a.ntail > 0;
+    const int km = a.kc - 1;
+    // carried-coast record: [0] backward start state, [1] state entering
+    // the segment, [2, 2 + kc) the end's states X, [2 + kc, 2 + 2 kc) the
+    // start's states S
     for (int it = 0; it < a.iters; ++it) {
         const float *src = it == 0 ? src0 : out;
         float st[3] = {0.f, 0.f, 0.f};
@@ -65,6 +76,7 @@ __global__ void __launch_bounds__(128) line_kernel(LineArgs a)
                 st[1] = x * s.y;
                 st[2] = x * s.z;
             }
+            if (car && sea && !prev_sea) st[0] = it == 0 ? 0.f : scr[nr * rk + 1];
             prev_sea = sea;
             out[k * ps] = step<ORDER, ADJ>(x, c, st);
             if (re && a.ntail > 0) {
@@ -75,6 +87,11 @@ __global__ void __launch_bounds__(128) line_kernel(LineArgs a)
                                         : m.x * st[0];
                 }
                 apply_tail<ORDER, ADJ>(a.tmap + 9 * rk, st, rec);
+                if (car) {
+                    rec[2 + it] = st[0];
+                    const float *mu = a.carry + 2 * km * rk;
+                    for (int d = 1; d <= it; ++d) rec[0] = fmaf(mu[d - 1], rec[2 + it - d], rec[0]);
+                }
                 if (cst && !ADJ) {
                     const float4 m = cv[2 * (rk - base)];
                     rec[0] = fmaf(x, m.x, rec[0]);
@@ -109,6 +126,16 @@ __global__ void __launch_bounds__(128) line_kernel(LineArgs a)
                 const float4 s = cv[2 * (rk - base) + 1];
                 y = fmaf(s.x, st[0], y);
                 if (ORDER == 3) y = fmaf(s.y, st[1], fmaf(s.z, st[2], y));
+            }
+            if (car && c.x != 0.f && (k == 0 || cf[k - 1].x == 0.f) && it + 1 < a.kc) {
+                // the segment's first point: keep S and form the next
+                // iteration's entering state
+                float *rec = scr + nr * rk;
+                rec[2 + a.kc + it] = st[0];
+                const float *lam = a.carry + 2 * km * rk + km;
+                float h = 0.f;
+                for (int d = 1; d <= it + 1; ++d) h = fmaf(lam[d - 1], rec[2 + a.kc + it + 1 - d], h);
+                rec[1] = h;
             }
             out[k * ps] = y;
         }

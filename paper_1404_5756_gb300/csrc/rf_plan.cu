@@ -64,6 +64,8 @@ struct Dir {
     float2 *tmap = nullptr;          // [ntail][9] hi/lo pairs, consecutive along each line
     float4 *cvec = nullptr;          // [ntail][2] (m, s) of constant-extension coasts
     bool cst = false;                // constant-extension coasts in force
+    int kc = 0;                      // carried coasts: K (0: not in force)
+    float *carry = nullptr;          // [2 fwd/adj][ntail][2 mu/lambda][K - 1] history weights
     int P = 32;                      // lanes per line of the tile kernel (32 or 16)
     float *xfer = nullptr;           // [ncl][nlines][P][XF]
     float4 *coef_il_base = nullptr;  // interleaved coefficients with guards
@@ -150,6 +152,7 @@ void free_domain(Domain &d)
         cudaFree(q.tail_base);
         cudaFree(q.tmap);
         cudaFree(q.cvec);
+        cudaFree(q.carry);
         cudaFree(q.xfer);
         cudaFree(q.coef_il_base);
         cudaFree(q.lanes);
@@ -182,9 +185,10 @@ rf_status check_options(const rf_options &o)
     if (o.iters < 1 || (o.order == 3 && o.iters != 1)) return RF_EINVAL;
     if (!(o.img_factor >= 0.0)) return RF_EINVAL;   // NaN or negative; +inf is allowed
     if (o.norm != RF_NORM_GAUSS_PEAK && o.norm != RF_NORM_UNIT_SUM) return RF_EINVAL;
-    if ((o.flags & ~(RF_FLAG_Q_CORRECTED | RF_FLAG_COAST_CONSTANT)) != 0 || o.chunk < 0 ||
-        o.tile < 0)
+    if ((o.flags & ~(RF_FLAG_Q_CORRECTED | RF_FLAG_COAST_CONSTANT | RF_FLAG_COAST_CARRIED)) != 0 ||
+        o.chunk < 0 || o.tile < 0)
         return RF_EINVAL;
+    if ((o.flags & RF_FLAG_COAST_CONSTANT) && (o.flags & RF_FLAG_COAST_CARRIED)) return RF_EINVAL;
     // the kernels derive chunk lengths and tile shapes from the line length
     // (the autotuner picks launch shapes); no override is built
     if (o.chunk != 0 || o.tile != 0) return RF_EUNSUPPORTED;
@@ -212,11 +216,21 @@ bool plan_cst(const rf_plan_ *p)
     return (p->opt.flags & RF_FLAG_COAST_CONSTANT) && p->opt.img_factor > 0.0;
 }
 
-// Floats per segment-end record of the kernels: the start state, plus the
-// last input (forward) or the tail-vector term (adjoint) with constant coasts.
+// Carried coasts in force: the option, the 1st-RF with more than one
+// iteration, and imaginary points to carry values.
+bool plan_carry(const rf_plan_ *p)
+{
+    return (p->opt.flags & RF_FLAG_COAST_CARRIED) && p->opt.order == 1 && p->opt.iters > 1 &&
+           p->opt.img_factor > 0.0;
+}
+
+// Floats per segment-end record of the long-line kernel: the start state,
+// plus the last input (forward) or the tail-vector term (adjoint) with
+// constant coasts; with carried coasts the start state, the state entering
+// the segment and the K boundary states of each end.
 int rec_floats(const Dir &q)
 {
-    return q.cst ? 4 : 3;
+    return q.kc > 0 ? 2 + 2 * q.kc : q.cst ? 4 : 3;
 }
 
 rf_status cuda_status(cudaError_t e)
@@ -637,8 +651,8 @@ RegShape reg_shape_for(const rf_plan_ *p, const Domain &D, const Dir &q, int dir
     for (const RegShape &s : kRegShapes)
         if (s.P == P && s.C >= need && (best.P == 0 || s.C < best.C)) best = s;
     if (best.P == 0) return best;
-    if (reg_smem_bytes(dir, p->opt.order, best.C, best.P, kRegWarps, q.max_ends, kRegPairs) >
-        (int64_t)kSmemMax)
+    if (reg_smem_bytes(dir, p->opt.order, best.C, best.P, kRegWarps, q.max_ends, kRegPairs,
+                       plan_carry(p) ? 2 + 2 * p->opt.iters : 0) > (int64_t)kSmemMax)
         return RegShape{0, 0};
     return best;
 }
@@ -716,6 +730,29 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
         if (s == RF_OK) s = cuda_status(cudaStreamSynchronize(st));
         cudaFree(dsp);
         RF_TRY(s);
+    }
+    if (plan_carry(P) && q.ntail > 0) {
+        // history weights of the carried coasts, FP64 on the host (the
+        // infinite imaginary sea is cut where the oracle cuts it)
+        q.kc = K;
+        const int km = K - 1;
+        std::vector<float> hw((size_t)(4 * q.ntail * km));
+        std::vector<double> buf, w((size_t)km);
+        for (int adj = 0; adj < 2; ++adj)
+            for (int64_t i = 0; i < q.ntail; ++i)
+                for (int side = 0; side < 2; ++side) {   // 0: the end (mu), 1: the start (lambda)
+                    const double sg = side == 0 ? sp[(size_t)i].sigma : sp[(size_t)i].sigma_h;
+                    const int ni = side == 0 ? sp[(size_t)i].n_img : sp[(size_t)i].n_h;
+                    const int64_t n = ni < 0 ? (int64_t)std::ceil(60.0 * (1.0 + 2.0 * sg)) : ni;
+                    buf.resize((size_t)(2 * n + 2));
+                    carry_weights_fp64(sg, n, K, nm, adj != 0, side == 0, buf.data(), w.data());
+                    for (int d = 0; d < km; ++d)
+                        hw[(((size_t)adj * q.ntail + i) * 2 + side) * km + d] = (float)w[(size_t)d];
+                }
+        RF_TRY(dev_alloc(&q.carry, (int64_t)hw.size(), &P->bytes));
+        RF_TRY(cuda_status(cudaMemcpyAsync(q.carry, hw.data(), hw.size() * sizeof(float),
+                                           cudaMemcpyHostToDevice, st)));
+        RF_TRY(cuda_status(cudaStreamSynchronize(st)));   // hw is released below
     }
     return RF_OK;
 }
@@ -812,10 +849,15 @@ bool reg_cfg(const Dir &q, int64_t nvar, int64_t nk, LaunchCfg &L)
     if ((q.dir == 0 ? (ngroups + kRegWarps - 1) / kRegWarps : ngroups) > 65535) return false;
     L = LaunchCfg{};
     L.reg = true;
+    const bool car = ORDER == 1 && q.kc > 0;
     L.smem = (size_t)reg_smem_bytes(q.dir, ORDER, q.rsh.C, q.rsh.P, kRegWarps, q.max_ends,
-                                    kRegPairs);
-    L.occ = q.dir == 0 ? reg_occupancy<ORDER, ADJ, 0>(q.rsh, L.smem)
-                       : reg_occupancy<ORDER, ADJ, 1>(q.rsh, L.smem);
+                                    kRegPairs, car ? 2 + 2 * q.kc : 0);
+    if (car)
+        L.occ = q.dir == 0 ? reg_occupancy<1, ADJ, 0, true>(q.rsh, L.smem)
+                           : reg_occupancy<1, ADJ, 1, true>(q.rsh, L.smem);
+    else
+        L.occ = q.dir == 0 ? reg_occupancy<ORDER, ADJ, 0>(q.rsh, L.smem)
+                           : reg_occupancy<ORDER, ADJ, 1>(q.rsh, L.smem);
     return L.occ > 0;
 }
 
@@ -830,6 +872,7 @@ LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk)
         LaunchCfg L;
         if (reg_cfg<ORDER, ADJ>(q, nvar, nk, L)) return L;
     }
+    if (q.kc > 0) return LaunchCfg{};   // carried coasts: the long-line kernel
     const int64_t ss = smem_stride(q.n);
     for (int pass = 0; pass < 2; ++pass) {
         const size_t cap = pass == 0 ? kSmemTarget : kSmemMax;
@@ -857,6 +900,10 @@ std::vector<LaunchCfg> launch_candidates(const Domain &D, const Dir &q, int64_t 
         LaunchCfg L;
         if (reg_cfg<ORDER, ADJ>(q, nvar, nk, L)) {
             out.push_back(L);
+            return out;
+        }
+        if (q.kc > 0) {   // carried coasts: the long-line kernel only
+            out.push_back(LaunchCfg{});
             return out;
         }
     }
@@ -965,8 +1012,17 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
         a.iters = iters;
         a.zero = 0;
         a.status = D.status;
-        if (q.dir == 0) reg_launch<ORDER, ADJ, 0>(a, q.rsh, L.smem, st);
-        else reg_launch<ORDER, ADJ, 1>(a, q.rsh, L.smem, st);
+        const bool car = ORDER == 1 && q.kc > 0;
+        a.kc = q.kc;
+        a.rs = car ? 2 + 2 * q.kc : (ORDER == 3 ? 3 : 1);
+        a.carry = car ? q.carry + (ADJ ? 2 * (q.kc - 1) * q.ntail : 0) : nullptr;
+        if (car) {
+            if (q.dir == 0) reg_launch<1, ADJ, 0, true>(a, q.rsh, L.smem, st);
+            else reg_launch<1, ADJ, 1, true>(a, q.rsh, L.smem, st);
+        } else {
+            if (q.dir == 0) reg_launch<ORDER, ADJ, 0>(a, q.rsh, L.smem, st);
+            else reg_launch<ORDER, ADJ, 1>(a, q.rsh, L.smem, st);
+        }
     } else if (L.tile) {
         const TileArgs a = tile_args(D, q, in, out, nvar, k0, nk, iters, L.nbuf);
         launch_shape<ORDER, ADJ>(a, L.sh, q.cst, q.nlines, L.groups, L.smem, st);
@@ -980,6 +1036,8 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
         a.cvec = q.cst ? q.cvec : nullptr;
         a.nr = rec_floats(q);
         a.tscr = D.tscr;
+        a.kc = q.kc;
+        a.carry = q.kc > 0 ? q.carry + (ADJ ? 2 * (q.kc - 1) * q.ntail : 0) : nullptr;
         a.n = q.n;
         a.nlines = q.nlines;
         a.pt_stride = q.pt_stride;
@@ -1028,8 +1086,8 @@ rf_status apply_domain(rf_plan_ *p, Domain &D, const float *in, float *out, int 
     for (int dir = 0; dir < 2; ++dir)
         if (line_path(cfg_of(p, D, dir, nvar, nkb, adjoint)) ||
             line_path(cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint)))
-            nt = std::max(nt, D.d[dir].ntail);
-    rf_status s = ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 4, &p->bytes);
+            nt = std::max(nt, D.d[dir].ntail * (int64_t)rec_floats(D.d[dir]));
+    rf_status s = ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt, &p->bytes);
     if (s != RF_OK) return s;
     const int K = p->opt.iters;
     for (int64_t k0 = 0; k0 < nz; k0 += nkb) {
@@ -1074,7 +1132,7 @@ bool multi_fits(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, size_t *
     bool any = false;
     for (const Domain &D : p->dom) {
         const Dir &q = D.d[dir];
-        if (q.R == 0 || q.P != sh.P || q.rsh.P > 0) continue;   // launched on their own
+        if (q.R == 0 || q.P != sh.P || q.rsh.P > 0 || q.kc > 0) continue;   // launched on their own
         m = std::max(m, (size_t)tile_smem_bytes(sh.R, sh.B, smem_stride(q.n), q.max_re, 1,
                                                 rec_floats(q)));
         any = true;
@@ -1135,7 +1193,8 @@ rf_status multi_pass(rf_plan_ *p, const MultiCfg &c, const float *const *src,
 {
     std::vector<int> doms;
     for (size_t d = 0; d < p->dom.size(); ++d)
-        if (p->dom[d].d[c.dir].R > 0 && p->dom[d].d[c.dir].P == c.P && p->dom[d].d[c.dir].rsh.P == 0)
+        if (p->dom[d].d[c.dir].R > 0 && p->dom[d].d[c.dir].P == c.P && p->dom[d].d[c.dir].rsh.P == 0 &&
+            p->dom[d].d[c.dir].kc == 0)
             doms.push_back((int)d);
     const int iters = p->opt.order == 3 ? 1 : p->opt.iters;
     const size_t nlaunch = (doms.size() + kMaxMulti - 1) / kMaxMulti;
@@ -1191,7 +1250,7 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
     // domains no multi-domain launch covers (lines too long for the tile
     // kernel, or no shape fits) launch on their own
     auto covered = [&](const Dir &q, int dir) {
-        if (q.R == 0 || q.rsh.P > 0) return false;   // register-kernel domains launch on their own
+        if (q.R == 0 || q.rsh.P > 0 || q.kc > 0) return false;   // register-kernel and carried-coast domains launch on their own
         for (int k = 0; k < nP; ++k)
             if (cs[dir][k].occ > 0 && cs[dir][k].P == q.P) return true;
         return false;
@@ -1202,9 +1261,9 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
             const Dir &q = D.d[dir];
             if (covered(q, dir)) continue;
             if (q.R == 0 || line_path(cfg_of(p, D, dir, nvar, D.g.nz, adjoint)))
-                nt = std::max(nt, q.ntail);
+                nt = std::max(nt, q.ntail * (int64_t)rec_floats(q));
         }
-        RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * D.g.nz * nt * 4, &p->bytes));
+        RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * D.g.nz * nt, &p->bytes));
     }
     if (dry) return RF_OK;
     const int K = p->opt.iters;
@@ -1486,8 +1545,8 @@ rf_status host_pipeline(rf_plan_ *p, Domain &D, const float *in, float *out, int
     for (int dir = 0; dir < 2; ++dir)
         if (line_path(cfg_of(p, D, dir, nvar, nkb, adjoint)) ||
             line_path(cfg_of(p, D, dir, nvar, nz - (nz - 1) / nkb * nkb, adjoint)))
-            nt = std::max(nt, D.d[dir].ntail);
-    RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt * 4, &p->bytes));
+            nt = std::max(nt, D.d[dir].ntail * (int64_t)rec_floats(D.d[dir]));
+    RF_TRY(ensure(&D.tscr, &D.tscr_floats, (int64_t)nvar * nz * nt, &p->bytes));
     const size_t pitch = (size_t)(nz * plane) * sizeof(float);
     const int K = p->opt.iters;
     // (a domain's stage is free here: every earlier host-buffer call ended
@@ -1710,6 +1769,8 @@ rf_status rf_apply_static(rf_plan p, const float *const *in, float *const *out, 
             a.cvec = q.cst ? q.cvec : nullptr;
             a.nr = rec_floats(q);
             a.tscr = scr;
+            a.kc = q.kc;
+            a.carry = q.kc > 0 ? q.carry + (adj ? 2 * (q.kc - 1) * q.ntail : 0) : nullptr;
             a.n = q.n;
             a.nlines = q.nlines;
             a.pt_stride = q.pt_stride;
@@ -1839,7 +1900,7 @@ rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
     char line[256];
     std::snprintf(line, sizeof line, "filter: order %d, K %d, img_factor %g, coasts %s%s\n",
                   p->opt.order, p->opt.iters, p->opt.img_factor,
-                  plan_cst(p) ? "constant extension" : "zero input",
+                  plan_cst(p) ? "constant extension" : plan_carry(p) ? "carried across iterations" : "zero input",
                   (p->opt.flags & RF_FLAG_Q_CORRECTED) ? ", q-corrected" : "");
     t += line;
     for (size_t d = 0; d < p->dom.size(); ++d) {

@@ -79,7 +79,18 @@ struct RegArgs {
                               // compiler cannot merge their loads (which would keep every
                               // coefficient of the chunk in registers across the sweeps)
     unsigned *status;         // device status word: bit 0 set if a bounded wait gave up
+    // carried coasts (1st-RF, CARRY kernels): per segment [2][kc - 1] (mu at
+    // its end, lambda at its start) of this direction, in boundary-map order
+    const float *carry;
+    int kc;                   // K
+    int rs;                   // 64-bit record values per (segment, pair): NS, or 2 + 2 kc
 };
+
+// Record of one (segment, pair) in the carried-coast kernels: [0] the state
+// recorded at the segment's end, then its start state M X + sum mu X; [1]
+// the state entering the segment; [2, 2 + kc) the end's states of the
+// iterations; [2 + kc, 2 + 2 kc) the start's states.
+constexpr int kRecEnter = 1, kRecX = 2;
 
 // Shared-memory layout of the register kernel (bytes):
 //   16 bytes: the mbarrier of the coefficient copy;
@@ -106,10 +117,11 @@ __host__ __device__ inline int64_t reg_stage_bytes(int dir, int C, int P, int NW
                     : (int64_t)SG * NW * LPW * reg_pitch(C, P) * 4;
 }
 
+// rs: 64-bit record values per (segment, pair) (0: the state size NS).
 __host__ __device__ inline int64_t reg_smem_bytes(int dir, int order, int C, int P, int NW,
-                                                  int max_re, int npr)
+                                                  int max_re, int npr, int rs = 0)
 {
-    const int LPW = 32 / P, NS = order == 3 ? 3 : 1;
+    const int LPW = 32 / P, NS = rs > 0 ? rs : order == 3 ? 3 : 1;
     const int64_t rec = (int64_t)NW * LPW * (max_re > 0 ? max_re : 1) * npr * NS * 8;
     return 16 + reg_coef_bytes(dir, C, P, NW) + reg_stage_bytes(dir, C, P, NW, npr) + rec;
 }
@@ -196,13 +208,20 @@ __device__ __forceinline__ u64 rstep_a(u64 y, u64 b, u64 ne, u64 nc1, u64 nc2, u
 // after each segment end into rec[slot].  Anticausal direction: the state is
 // set from rec[slot] before a segment end is stepped.  slot counts segment
 // ends on the line: from rank0 up (causal) or down from rank0 + nre - 1
-// (anticausal).  Land (bit set in `land`) steps with g = 0.
-template <int ORDER, bool ADJ, bool CAUSAL, bool WRITE, bool REC, int C, int P, int NPR>
+// (anticausal).  Land (bit set in `land`) steps with g = 0.  CARRY (carried
+// coasts, first order; records of RS values): the causal sweeps set the state
+// from rec[slot][kRecEnter] before a segment start is stepped, and the
+// anticausal WRITE sweep records the state after each segment start into
+// rec[slot][soff].
+template <int ORDER, bool ADJ, bool CAUSAL, bool WRITE, bool REC, int C, int P, int NPR,
+          bool CARRY = false>
 __device__ __forceinline__ void rsweep(u64 (&x)[NPR][C], u64 (&st)[NPR][3],
                                        const float4 *__restrict__ cp, u64 ends, u64 land,
-                                       u64 *__restrict__ rec, int slot)
+                                       u64 *__restrict__ rec, int slot, u64 starts = 0ull,
+                                       int RS = ORDER == 3 ? 3 : 1, int soff = 0)
 {
     constexpr int NS = ORDER == 3 ? 3 : 1;
+    if (!CARRY) RS = NS;
     const u64 one = V2::bc(1.f);
 #pragma unroll
     for (int kk = 0; kk < C; ++kk) {
@@ -216,8 +235,12 @@ __device__ __forceinline__ void rsweep(u64 (&x)[NPR][C], u64 (&st)[NPR][3],
 #pragma unroll
             for (int p = 0; p < NPR; ++p)
 #pragma unroll
-                for (int q = 0; q < NS; ++q) st[p][q] = rec[(slot * NPR + p) * NS + q];
+                for (int q = 0; q < NS; ++q) st[p][q] = rec[(slot * NPR + p) * RS + q];
             --slot;
+        }
+        if (CARRY && CAUSAL && ((starts >> k) & 1ull)) {
+#pragma unroll
+            for (int p = 0; p < NPR; ++p) st[p][0] = rec[(slot * NPR + p) * RS + kRecEnter];
         }
 #pragma unroll
         for (int p = 0; p < NPR; ++p) {
@@ -225,11 +248,18 @@ __device__ __forceinline__ void rsweep(u64 (&x)[NPR][C], u64 (&st)[NPR][3],
                               : rstep_f<ORDER>(x[p][k], b, ne, nc1, nc2, g, st[p]);
             if (WRITE) x[p][k] = y;
         }
-        if (CAUSAL && REC && at_end) {
+        if (CARRY && !CAUSAL && WRITE && ((starts >> k) & 1ull)) {
+            // slot + 1 is the segment of this start (its end is passed)
 #pragma unroll
-            for (int p = 0; p < NPR; ++p)
+            for (int p = 0; p < NPR; ++p) rec[((slot + 1) * NPR + p) * RS + soff] = st[p][0];
+        }
+        if (CAUSAL && (REC || CARRY) && at_end) {
+            if (REC) {
 #pragma unroll
-                for (int q = 0; q < NS; ++q) rec[(slot * NPR + p) * NS + q] = st[p][q];
+                for (int p = 0; p < NPR; ++p)
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) rec[(slot * NPR + p) * RS + q] = st[p][q];
+            }
             ++slot;
         }
     }
@@ -307,34 +337,70 @@ __device__ __forceinline__ void rscan(float *Pm, u64 (&v)[NPR][3], int l)
 // q = l, l + P, ...; the recorded state of each slice becomes M X (adjoint
 // M^T X), applied in compensated FP32 (rf_steps.cuh).  Without imaginary
 // points (ml null) every start state is zero.
-template <int ORDER, bool ADJ, int P, int NPR>
+// CARRY (carried coasts, iteration it, records of RS values, mu the line's
+// history weights, kc - 1 per segment): the recorded state is also kept as
+// the iteration's X, and the start state gains sum_d mu_d X_{it-d}.
+template <int ORDER, bool ADJ, int P, int NPR, bool CARRY = false>
 __device__ __forceinline__ void rtails(u64 *__restrict__ rec, const float2 *__restrict__ ml,
-                                       int nre_line, int l)
+                                       int nre_line, int l, int RS = ORDER == 3 ? 3 : 1,
+                                       const float *__restrict__ mu = nullptr, int it = 0,
+                                       int kc = 1)
 {
     constexpr int NS = ORDER == 3 ? 3 : 1;
+    if (!CARRY) RS = NS;
     for (int q = l; q < nre_line; q += P) {
-        u64 *r = rec + q * NPR * NS;
+        u64 *r = rec + q * NPR * RS;
         if (!ml) {
 #pragma unroll
-            for (int k = 0; k < NPR * NS; ++k) r[k] = 0ull;
+            for (int p = 0; p < NPR; ++p)
+#pragma unroll
+                for (int k = 0; k < NS; ++k) r[p * RS + k] = 0ull;
             continue;
         }
 #pragma unroll
-        for (int p = 0; p < NPR; ++p)
+        for (int p = 0; p < NPR; ++p) {
+            if (CARRY) r[p * RS + kRecX + it] = r[p * RS];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 float X[3] = {0.f, 0.f, 0.f}, Y[3];
 #pragma unroll
-                for (int k = 0; k < NS; ++k) X[k] = V2::get(r[p * NS + k], h);
+                for (int k = 0; k < NS; ++k) X[k] = V2::get(r[p * RS + k], h);
                 apply_tail<ORDER, ADJ>(ml + 9 * q, X, Y);
 #pragma unroll
                 for (int k = 0; k < NS; ++k) {
-                    float lo = V2::get(r[p * NS + k], 0), hi = V2::get(r[p * NS + k], 1);
+                    float lo = V2::get(r[p * RS + k], 0), hi = V2::get(r[p * RS + k], 1);
                     if (h == 0) lo = Y[k];
                     else hi = Y[k];
-                    r[p * NS + k] = V2::pack(lo, hi);
+                    r[p * RS + k] = V2::pack(lo, hi);
                 }
             }
+            if (CARRY) {
+                const float *m = mu + (int64_t)q * 2 * (kc - 1);
+                u64 y = r[p * RS];
+                for (int d = 1; d <= it; ++d)
+                    y = V2::fma(V2::bc(m[d - 1]), r[p * RS + kRecX + it - d], y);
+                r[p * RS] = y;
+            }
+        }
+    }
+}
+
+// Carried coasts: the state entering each segment of the line in iteration
+// it + 1, sum_{d=1..it+1} lambda_d S_{it+1-d} (lam: the line's weights).
+template <int P, int NPR>
+__device__ __forceinline__ void rheads(u64 *__restrict__ rec, const float *__restrict__ lam,
+                                       int nre_line, int l, int RS, int it, int kc)
+{
+    for (int q = l; q < nre_line; q += P) {
+        u64 *r = rec + q * NPR * RS;
+        const float *w = lam + (int64_t)q * 2 * (kc - 1) + (kc - 1);
+#pragma unroll
+        for (int p = 0; p < NPR; ++p) {
+            u64 h = 0ull;
+            for (int d = 1; d <= it + 1; ++d)
+                h = V2::fma(V2::bc(w[d - 1]), r[p * RS + kRecX + kc + it + 1 - d], h);
+            r[p * RS + kRecEnter] = h;
+        }
     }
 }
 
@@ -391,10 +457,12 @@ constexpr int kRegWaitTries = 1 << 20;
 //   tile together.
 // Both: the CTA's coefficient block arrives by one bulk copy while the data
 // loads are in flight.
-template <int ORDER, bool ADJ, int DIR, int C, int P, int NW, int NPR>
+template <int ORDER, bool ADJ, int DIR, int C, int P, int NW, int NPR, bool CARRY = false>
 __global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const RegArgs a)
 {
     constexpr int NS = ORDER == 3 ? 3 : 1, MX = RXF<ORDER>::mat;
+    static_assert(!CARRY || ORDER == 1, "carried coasts are a first-order option");
+    const int RS = CARRY ? a.rs : NS;
     constexpr int LPW = 32 / P, R = NW * LPW, LC = DIR == 0 ? LPW : R;
     constexpr int STG = DIR == 0 ? LPW * P * (C + 4) : R * reg_pitch(C, P);   // floats per slice
     constexpr int PITCH = reg_pitch(C, P);
@@ -418,7 +486,7 @@ __global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const Re
     const int64_t myline0 = line0 + ql;
     const bool line_ok = myline0 < a.nlines;
     const int64_t line = line_ok ? myline0 : a.nlines - 1;   // past the end: compute, never store
-    u64 *rec = recs + ((int64_t)warp * LPW + ql) * (a.max_re > 0 ? a.max_re : 1) * NPR * NS;
+    u64 *rec = recs + ((int64_t)warp * LPW + ql) * (a.max_re > 0 ? a.max_re : 1) * NPR * RS;
 
     // coefficient block of the CTA's lines: one bulk copy
     if (threadIdx.x == 0) {
@@ -434,6 +502,8 @@ __global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const Re
     // segment ends on the line: the last lane's rank plus its own count
     const int nre_line = __shfl_sync(0xffffffffu, li.rank0 + li.nre, P - 1, P);
     const float2 *ml = a.tmap ? a.tmap + 9 * (int64_t)a.tail_base[line] : nullptr;
+    // carried coasts: the line's history weights (mu, lambda per segment)
+    const float *cw = CARRY ? a.carry + (int64_t)a.tail_base[line] * 2 * (a.kc - 1) : nullptr;
 
     int64_t off[SG];
     bool sok[SG];
@@ -577,6 +647,13 @@ __global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const Re
 
     // ------------------------------------------------------------ filter
     if (active) {
+        if (CARRY) {
+            // the first iteration enters every segment from zero
+            for (int q = l; q < nre_line; q += P)
+#pragma unroll
+                for (int p = 0; p < NPR; ++p) rec[(q * NPR + p) * RS + kRecEnter] = 0ull;
+            __syncwarp();
+        }
         for (int it = 0; it < a.iters; ++it) {
             u64 st[NPR][3];
             float Pm[MX];
@@ -585,31 +662,36 @@ __global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const Re
             for (int p = 0; p < NPR; ++p)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) st[p][q] = 0ull;
-            rsweep<ORDER, ADJ, true, false, false, C, P, NPR>(x, st, cp + a.zero, li.ends, li.land,
-                                                         rec, 0);
+            rsweep<ORDER, ADJ, true, false, false, C, P, NPR, CARRY>(
+                x, st, cp + a.zero, li.ends, li.land, rec, CARRY ? li.rank0 : 0, li.starts, RS);
 #pragma unroll
             for (int k = 0; k < MX; ++k) Pm[k] = __ldg(xf + k);
             rscan<ORDER, false, P, NPR>(Pm, st, l);
             // B: from the true state, recording segment ends
-            rsweep<ORDER, ADJ, true, true, true, C, P, NPR>(x, st, cp + 2 * a.zero, li.ends, li.land,
-                                                       rec, li.rank0);
+            rsweep<ORDER, ADJ, true, true, true, C, P, NPR, CARRY>(
+                x, st, cp + 2 * a.zero, li.ends, li.land, rec, li.rank0, li.starts, RS);
             __syncwarp();
-            if (line_ok) rtails<ORDER, ADJ, P, NPR>(rec, ml, nre_line, l);
+            if (line_ok) rtails<ORDER, ADJ, P, NPR, CARRY>(rec, ml, nre_line, l, RS, cw, it, a.kc);
             __syncwarp();
             // C: local anticausal-direction sweep
 #pragma unroll
             for (int p = 0; p < NPR; ++p)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) st[p][q] = 0ull;
-            rsweep<ORDER, ADJ, false, false, false, C, P, NPR>(x, st, cp + 3 * a.zero, li.ends,
-                                                          li.land, rec, li.rank0 + li.nre - 1);
+            rsweep<ORDER, ADJ, false, false, false, C, P, NPR, CARRY>(
+                x, st, cp + 3 * a.zero, li.ends, li.land, rec, li.rank0 + li.nre - 1, li.starts, RS);
 #pragma unroll
             for (int k = 0; k < MX; ++k) Pm[k] = __ldg(xf + MX + k);
             rscan<ORDER, true, P, NPR>(Pm, st, l);
-            // D: from the true state
-            rsweep<ORDER, ADJ, false, true, false, C, P, NPR>(x, st, cp + 4 * a.zero, li.ends,
-                                                         li.land, rec, li.rank0 + li.nre - 1);
+            // D: from the true state (carried coasts: recording segment starts)
+            rsweep<ORDER, ADJ, false, true, false, C, P, NPR, CARRY>(
+                x, st, cp + 4 * a.zero, li.ends, li.land, rec, li.rank0 + li.nre - 1, li.starts, RS,
+                kRecX + a.kc + it);
             __syncwarp();   // the records are rewritten by the next iteration's B
+            if (CARRY && it + 1 < a.iters) {
+                if (line_ok) rheads<P, NPR>(rec, cw, nre_line, l, RS, it, a.kc);
+                __syncwarp();
+            }
         }
     }
 

@@ -2,5 +2,5 @@
 #include "rf_reg_impl.cuh"
 
 namespace rfvh {
-RF_REG_INSTANTIATE(1, false, 0)
+RF_REG_INSTANTIATE(1, false, 0, false)
 }  // namespace rfvh

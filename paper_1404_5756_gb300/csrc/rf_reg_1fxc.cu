@@ -1,0 +1,7 @@
+// Register-resident kernel of the first-order filter with carried coasts,
+// forward steps, x pass (rows).
+#include "rf_reg_impl.cuh"
+
+namespace rfvh {
+RF_REG_INSTANTIATE(1, false, 0, true)
+}  // namespace rfvh

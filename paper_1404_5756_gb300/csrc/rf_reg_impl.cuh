@@ -13,7 +13,7 @@ namespace {
 // Raise a kernel's dynamic shared-memory limit once per device and size, so
 // a launch inside a stream capture makes no attribute call.
 constexpr int kRegAttrDevices = 64;
-template <int ORDER, bool ADJ, int DIR, int C, int P>
+template <int ORDER, bool ADJ, int DIR, int C, int P, bool CARRY>
 void reg_smem_attr(size_t smem)
 {
     static std::mutex mu;
@@ -22,7 +22,7 @@ void reg_smem_attr(size_t smem)
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
     if (dev >= 0 && dev < kRegAttrDevices && smem <= done[dev]) return;
-    cudaFuncSetAttribute(reg_kernel<ORDER, ADJ, DIR, C, P, kRegWarps, kRegPairs>,
+    cudaFuncSetAttribute(reg_kernel<ORDER, ADJ, DIR, C, P, kRegWarps, kRegPairs, CARRY>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < kRegAttrDevices) done[dev] = smem;
 }
@@ -31,13 +31,13 @@ void reg_smem_attr(size_t smem)
 
 #define RF_FOR_EACH_REG_SHAPE(X) X(24, 32) X(32, 32) X(24, 16) X(32, 16) X(16, 8) X(32, 8)
 
-template <int ORDER, bool ADJ, int DIR>
+template <int ORDER, bool ADJ, int DIR, bool CARRY>
 bool reg_launch(const RegArgs &a, RegShape sh, size_t smem, cudaStream_t st)
 {
 #define RF_REG_SHAPE(c, p)                                                                \
     if (sh.C == c && sh.P == p) {                                                         \
-        reg_smem_attr<ORDER, ADJ, DIR, c, p>(smem);                                       \
-        reg_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, kRegPairs>                           \
+        reg_smem_attr<ORDER, ADJ, DIR, c, p, CARRY>(smem);                                \
+        reg_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, kRegPairs, CARRY>                    \
             <<<reg_grid(DIR, sh, a.nlines, a.ngroups), kRegWarps * 32, smem, st>>>(a);    \
         return true;                                                                      \
     }
@@ -46,15 +46,15 @@ bool reg_launch(const RegArgs &a, RegShape sh, size_t smem, cudaStream_t st)
     return false;
 }
 
-template <int ORDER, bool ADJ, int DIR>
+template <int ORDER, bool ADJ, int DIR, bool CARRY>
 int reg_occupancy(RegShape sh, size_t smem)
 {
 #define RF_REG_SHAPE(c, p)                                                                 \
     if (sh.C == c && sh.P == p) {                                                          \
-        reg_smem_attr<ORDER, ADJ, DIR, c, p>(smem);                                        \
+        reg_smem_attr<ORDER, ADJ, DIR, c, p, CARRY>(smem);                                 \
         int blocks = 0;                                                                    \
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                 \
-                &blocks, reg_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, kRegPairs>,          \
+                &blocks, reg_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, kRegPairs, CARRY>,   \
                 kRegWarps * 32, smem)                                                      \
             != cudaSuccess) {                                                              \
             cudaGetLastError();                                                            \
@@ -69,8 +69,8 @@ int reg_occupancy(RegShape sh, size_t smem)
 
 #undef RF_FOR_EACH_REG_SHAPE
 
-#define RF_REG_INSTANTIATE(O, A, D)                                                   \
-    template bool reg_launch<O, A, D>(const RegArgs &, RegShape, size_t, cudaStream_t); \
-    template int reg_occupancy<O, A, D>(RegShape, size_t);
+#define RF_REG_INSTANTIATE(O, A, D, K)                                                   \
+    template bool reg_launch<O, A, D, K>(const RegArgs &, RegShape, size_t, cudaStream_t); \
+    template int reg_occupancy<O, A, D, K>(RegShape, size_t);
 
 }  // namespace rfvh

@@ -24,26 +24,31 @@ struct RegShape {
 // P C >= n.
 constexpr RegShape kRegShapes[] = {{24, 32}, {32, 32}, {24, 16}, {32, 16}, {16, 8}, {32, 8}};
 
-// Launch one pass.  Returns false if (C, P) is not built.
-template <int ORDER, bool ADJ, int DIR>
+// Launch one pass.  Returns false if (C, P) is not built.  CARRY: the
+// carried-coast kernels (first order only, in their own translation units).
+template <int ORDER, bool ADJ, int DIR, bool CARRY = false>
 bool reg_launch(const RegArgs &a, RegShape sh, size_t smem, cudaStream_t st);
 
 // Resident CTAs per SM with `smem` bytes of dynamic shared memory (0: cannot
 // run or not built).
-template <int ORDER, bool ADJ, int DIR>
+template <int ORDER, bool ADJ, int DIR, bool CARRY = false>
 int reg_occupancy(RegShape sh, size_t smem);
 
-#define RF_REG_DECLARE(O, A, D)                                                              \
-    extern template bool reg_launch<O, A, D>(const RegArgs &, RegShape, size_t, cudaStream_t); \
-    extern template int reg_occupancy<O, A, D>(RegShape, size_t);
-RF_REG_DECLARE(3, false, 0)
-RF_REG_DECLARE(3, false, 1)
-RF_REG_DECLARE(3, true, 0)
-RF_REG_DECLARE(3, true, 1)
-RF_REG_DECLARE(1, false, 0)
-RF_REG_DECLARE(1, false, 1)
-RF_REG_DECLARE(1, true, 0)
-RF_REG_DECLARE(1, true, 1)
+#define RF_REG_DECLARE(O, A, D, K)                                                               \
+    extern template bool reg_launch<O, A, D, K>(const RegArgs &, RegShape, size_t, cudaStream_t); \
+    extern template int reg_occupancy<O, A, D, K>(RegShape, size_t);
+RF_REG_DECLARE(3, false, 0, false)
+RF_REG_DECLARE(3, false, 1, false)
+RF_REG_DECLARE(3, true, 0, false)
+RF_REG_DECLARE(3, true, 1, false)
+RF_REG_DECLARE(1, false, 0, false)
+RF_REG_DECLARE(1, false, 1, false)
+RF_REG_DECLARE(1, true, 0, false)
+RF_REG_DECLARE(1, true, 1, false)
+RF_REG_DECLARE(1, false, 0, true)
+RF_REG_DECLARE(1, false, 1, true)
+RF_REG_DECLARE(1, true, 0, true)
+RF_REG_DECLARE(1, true, 1, true)
 #undef RF_REG_DECLARE
 
 // Grid of a pass: x: (row blocks of 32/P rows, slice groups / warps per

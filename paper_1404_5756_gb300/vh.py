@@ -25,16 +25,19 @@ class Options:
     img_factor: float = 3.0
     norm: int = _lib.RF_NORM_GAUSS_PEAK
     qcorr: bool = False     # q-corrected 3rd-RF: impulse variance sigma^2
-    coast: str = "zero"     # imaginary points carry "zero" or the edge value ("constant")
+    # imaginary points carry "zero", the edge value ("constant"), or zero at
+    # first and then their own values across the 1st-RF iterations ("carried")
+    coast: str = "zero"
 
     def to_c(self) -> _lib.rf_options:
-        if self.coast not in ("zero", "constant"):
-            raise ValueError(f"coast must be 'zero' or 'constant', not {self.coast!r}")
+        flag = {"zero": 0, "constant": _lib.RF_FLAG_COAST_CONSTANT,
+                "carried": _lib.RF_FLAG_COAST_CARRIED}
+        if self.coast not in flag:
+            raise ValueError(f"coast must be 'zero', 'constant' or 'carried', not {self.coast!r}")
         o = _lib.rf_options_default()
         o.order, o.iters = int(self.order), int(self.iters)
         o.img_factor, o.norm = float(self.img_factor), int(self.norm)
-        o.flags = ((_lib.RF_FLAG_Q_CORRECTED if self.qcorr else 0)
-                   | (_lib.RF_FLAG_COAST_CONSTANT if self.coast == "constant" else 0))
+        o.flags = (_lib.RF_FLAG_Q_CORRECTED if self.qcorr else 0) | flag[self.coast]
         return o
 
 

@@ -67,9 +67,11 @@ def test_rf_coeffs_rejects_bad_arguments(lib):
         return o
     for o in [with_(order=2), with_(order=3, iters=2), with_(order=1, iters=0),
               with_(img_factor=-1.0), with_(img_factor=float("-inf")),
-              with_(img_factor=float("nan")), with_(norm=5), with_(flags=4),
+              with_(img_factor=float("nan")), with_(norm=5), with_(flags=8),
               with_(chunk=-1), with_(tile=-3),
               with_(flags=_lib.RF_FLAG_COAST_CONSTANT | 8),
+              with_(order=1, iters=5,
+                    flags=_lib.RF_FLAG_COAST_CONSTANT | _lib.RF_FLAG_COAST_CARRIED),
               with_(order=1, iters=5, flags=_lib.RF_FLAG_Q_CORRECTED),
               with_(order=1, iters=5,
                     flags=_lib.RF_FLAG_Q_CORRECTED | _lib.RF_FLAG_COAST_CONSTANT)]:
@@ -121,13 +123,15 @@ def test_product_path_has_no_oracle_dependency():
 
 def test_python_options_map_to_the_c_flags(lib):
     """Options -> rf_options: the q-correction and the coast treatment become
-    RF_FLAG_Q_CORRECTED and RF_FLAG_COAST_CONSTANT, and the C header carries
-    the same values the binding uses."""
+    RF_FLAG_Q_CORRECTED, RF_FLAG_COAST_CONSTANT and RF_FLAG_COAST_CARRIED, and
+    the C header carries the same values the binding uses."""
     from paper_1404_5756_gb300 import Options
     hdr = open(_lib.HEADER).read()
     assert "RF_FLAG_Q_CORRECTED = 1" in hdr and "RF_FLAG_COAST_CONSTANT = 2" in hdr
+    assert "RF_FLAG_COAST_CARRIED = 4" in hdr
     cases = [(dict(), 0), (dict(qcorr=True), _lib.RF_FLAG_Q_CORRECTED),
              (dict(coast="constant"), _lib.RF_FLAG_COAST_CONSTANT),
+             (dict(coast="carried"), _lib.RF_FLAG_COAST_CARRIED),
              (dict(qcorr=True, coast="constant"),
               _lib.RF_FLAG_Q_CORRECTED | _lib.RF_FLAG_COAST_CONSTANT)]
     for kw, flags in cases:
