@@ -551,6 +551,17 @@ def run_gpu(args):
     value_c = world * 2 * npts / (tc_ms / max(3, min(args.steps, 10)) * 1e-3) / 1e9
     plan_c.close()
 
+    # ---- 1st-RF x5 with carried coasts (an option), same protocol, fewer steps
+    plan_k = Plan(dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=nz),
+                  Options(order=1, iters=5, coast="carried"), device=dev)
+    plan_k.tune(nvar)
+    barrier()
+    tk_ms, _, _, _ = timed_loop(torch, plan_k, x, y, z, max(3, min(args.steps, 10)),
+                                args.warmup, stream, "rf1k_timed")
+    tk_ms = max_over_ranks(torch, world, tk_ms)
+    value_k = world * 2 * npts / (tk_ms / max(3, min(args.steps, 10)) * 1e-3) / 1e9
+    plan_k.close()
+
     # ---- end to end through the C ABI on pinned host buffers
     bound = bind_to_gpu_numa_node(torch, dev)
     xh = torch.from_numpy(w["x"]).pin_memory()
@@ -632,6 +643,9 @@ def run_gpu(args):
                       "note": "q-corrected 3rd-RF (impulse variance sigma^2), same protocol"},
         "rf3_coast_constant": {"value": value_c, "unit": "Gpts/s",
                                "note": "3rd-RF with constant-extension coasts, same protocol"},
+        "rf1x5_coast_carried": {"value": value_k, "unit": "Gpts/s",
+                                "note": "1st-RF x5 with imaginary values carried between the "
+                                        "iterations, same protocol"},
         "ragged64": ragged,
         "configs": configs,
         "clocks": clk.summary(),

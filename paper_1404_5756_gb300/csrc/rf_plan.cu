@@ -637,19 +637,23 @@ constexpr TileShape kShapesX[] = {
     {16, 8, 32}, {4, 4, 16},  {8, 4, 16},  {16, 4, 16}, {8, 8, 16},  {16, 8, 16},
     {8, 2, 16},  {16, 2, 16}, {8, 1, 16}};
 
-// Chunking of the register-resident kernel for one direction: P = 32 lanes
-// per line for lines of 513..1024 points, 16 for 257..512, 8 below, and the
-// smallest built chunk length C with P C >= n.  None (P = 0) for per-level
-// coefficients, constant-extension coasts, longer lines, or segment-end
-// records that do not fit shared memory.
+// Chunking of the register-resident kernel for one direction: the first
+// built shape (kRegShapes) with P C >= n.  None (P = 0) for per-level
+// coefficients, constant-extension coasts, longer lines, segment-end
+// records that do not fit shared memory, and the third-order y pass (whose
+// column strips the tile kernel filters faster: measured on the regional
+// and the ragged batches).  The choice depends on the line and the options
+// alone, never on tuning or batching.
 RegShape reg_shape_for(const rf_plan_ *p, const Domain &D, const Dir &q, int dir)
 {
     if (D.ncl != 1 || plan_cst(p) || q.n > 1024) return RegShape{0, 0};
-    const int P = q.n > 512 ? 32 : q.n > 256 ? 16 : 8;
-    const int64_t need = (q.n + P - 1) / P;
+    if (p->opt.order == 3 && dir == 1) return RegShape{0, 0};
     RegShape best{0, 0};
     for (const RegShape &s : kRegShapes)
-        if (s.P == P && s.C >= need && (best.P == 0 || s.C < best.C)) best = s;
+        if ((int64_t)s.C * s.P >= q.n) {
+            best = s;
+            break;
+        }
     if (best.P == 0) return best;
     if (reg_smem_bytes(dir, p->opt.order, best.C, best.P, kRegWarps, q.max_ends, kRegPairs,
                        plan_carry(p) ? 2 + 2 * p->opt.iters : 0) > (int64_t)kSmemMax)
@@ -984,38 +988,49 @@ TileArgs tile_args(const Domain &D, const Dir &q, const float *in, float *out, i
     return a;
 }
 
+// Arguments of the register kernel for one pass of one domain.
+template <int ORDER, bool ADJ>
+RegArgs reg_args(const Domain &D, const Dir &q, const float *in, float *out, int64_t nvar,
+                 int64_t k0, int64_t nk, int iters)
+{
+    const int64_t plane = D.g.nx * D.g.ny;
+    RegArgs a{};
+    a.in = in;
+    a.out = out;
+    a.coef = q.rcoef;
+    a.lanes = q.rlanes;
+    a.xfer = q.rxfer;
+    a.tail_base = q.tail_base;
+    a.tmap = q.ntail > 0 ? q.tmap : nullptr;
+    a.n = q.n;
+    a.nlines = q.nlines;
+    a.nx = D.g.nx;
+    a.plane = plane;
+    a.nz = D.g.nz;
+    a.k0 = k0;
+    a.nk = nk;
+    a.nslices = nvar * nk;
+    a.ngroups = (a.nslices + 2 * kRegPairs - 1) / (2 * kRegPairs);
+    a.max_re = q.max_ends;
+    a.vec4 = D.g.nx % 4 == 0 && ((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0;
+    a.iters = iters;
+    a.zero = 0;
+    a.status = D.status;
+    const bool car = ORDER == 1 && q.kc > 0;
+    a.kc = q.kc;
+    a.rs = car ? 2 + 2 * q.kc : (ORDER == 3 ? 3 : 1);
+    a.carry = car ? q.carry + (ADJ ? 2 * (q.kc - 1) * q.ntail : 0) : nullptr;
+    return a;
+}
+
 template <int ORDER, bool ADJ>
 void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *in,
                 float *out, int64_t nvar, int64_t k0, int64_t nk, int iters, cudaStream_t st)
 {
     const int64_t plane = D.g.nx * D.g.ny;
     if (L.reg) {
-        RegArgs a{};
-        a.in = in;
-        a.out = out;
-        a.coef = q.rcoef;
-        a.lanes = q.rlanes;
-        a.xfer = q.rxfer;
-        a.tail_base = q.tail_base;
-        a.tmap = q.ntail > 0 ? q.tmap : nullptr;
-        a.n = q.n;
-        a.nlines = q.nlines;
-        a.nx = D.g.nx;
-        a.plane = plane;
-        a.nz = D.g.nz;
-        a.k0 = k0;
-        a.nk = nk;
-        a.nslices = nvar * nk;
-        a.ngroups = (a.nslices + 2 * kRegPairs - 1) / (2 * kRegPairs);
-        a.max_re = q.max_ends;
-        a.vec4 = D.g.nx % 4 == 0 && ((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0;
-        a.iters = iters;
-        a.zero = 0;
-        a.status = D.status;
+        const RegArgs a = reg_args<ORDER, ADJ>(D, q, in, out, nvar, k0, nk, iters);
         const bool car = ORDER == 1 && q.kc > 0;
-        a.kc = q.kc;
-        a.rs = car ? 2 + 2 * q.kc : (ORDER == 3 ? 3 : 1);
-        a.carry = car ? q.carry + (ADJ ? 2 * (q.kc - 1) * q.ntail : 0) : nullptr;
         if (car) {
             if (q.dir == 0) reg_launch<1, ADJ, 0, true>(a, q.rsh, L.smem, st);
             else reg_launch<1, ADJ, 1, true>(a, q.rsh, L.smem, st);
@@ -1234,6 +1249,81 @@ rf_status multi_pass(rf_plan_ *p, const MultiCfg &c, const float *const *src,
     return RF_OK;
 }
 
+// One pass of the register-kernel domains of a batch: one launch per chunk
+// shape (C, P) over all domains of that shape (in groups of kRegMulti), the
+// CTAs of every domain's grid concatenated.
+template <int ORDER, bool ADJ>
+rf_status reg_multi_group(rf_plan_ *p, int dir, const std::vector<size_t> &ds,
+                          const float *const *src, float *const *out, int nvar, cudaStream_t st)
+{
+    RegMulti m{};
+    const RegShape sh = p->dom[ds[0]].d[dir].rsh;
+    const bool car = ORDER == 1 && p->dom[ds[0]].d[dir].kc > 0;
+    size_t smem = 0;
+    m.nd = (int)ds.size();
+    m.cta0[0] = 0;
+    for (int i = 0; i < m.nd; ++i) {
+        const Domain &D = p->dom[ds[(size_t)i]];
+        const Dir &q = D.d[dir];
+        m.dom[i] = reg_args<ORDER, ADJ>(D, q, src[ds[(size_t)i]], out[ds[(size_t)i]], nvar, 0,
+                                        D.g.nz, ORDER == 3 ? 1 : p->opt.iters);
+        const dim3 g = reg_grid(dir, sh, m.dom[i].nlines, m.dom[i].ngroups);
+        m.gx[i] = (int)g.x;
+        m.cta0[i + 1] = m.cta0[i] + (int64_t)g.x * g.y;
+        smem = std::max(smem, (size_t)reg_smem_bytes(dir, ORDER, sh.C, sh.P, kRegWarps, q.max_ends,
+                                                     kRegPairs, car ? 2 + 2 * q.kc : 0));
+    }
+    if (m.cta0[m.nd] > INT32_MAX) return RF_EINVAL;
+    const unsigned grid = (unsigned)m.cta0[m.nd];
+    if (car) {
+        if (dir == 0) reg_launch_multi<1, ADJ, 0, true>(m, sh, smem, grid, st);
+        else reg_launch_multi<1, ADJ, 1, true>(m, sh, smem, grid, st);
+    } else {
+        if (dir == 0) reg_launch_multi<ORDER, ADJ, 0>(m, sh, smem, grid, st);
+        else reg_launch_multi<ORDER, ADJ, 1>(m, sh, smem, grid, st);
+    }
+    const rf_status s = cuda_status(cudaGetLastError());
+    if (s != RF_OK) {
+        if (p->sticky == RF_OK) p->sticky = s;
+        return s;
+    }
+    ++p->launches;
+    return RF_OK;
+}
+
+rf_status reg_multi_pass(rf_plan_ *p, int dir, const float *const *src, float *const *out,
+                         int nvar, bool adjoint, cudaStream_t st)
+{
+    // domains grouped by chunk shape, in plan order
+    std::vector<std::pair<std::pair<int, int>, std::vector<size_t>>> groups;
+    for (size_t d = 0; d < p->dom.size(); ++d) {
+        const RegShape sh = p->dom[d].d[dir].rsh;
+        if (sh.P == 0) continue;
+        auto it = std::find_if(groups.begin(), groups.end(),
+                               [&](const auto &g) { return g.first == std::make_pair(sh.C, sh.P); });
+        if (it == groups.end()) {
+            groups.push_back({{sh.C, sh.P}, {}});
+            it = groups.end() - 1;
+        }
+        it->second.push_back(d);
+    }
+    for (const auto &g : groups)
+        for (size_t i0 = 0; i0 < g.second.size(); i0 += kRegMulti) {
+            const std::vector<size_t> ds(g.second.begin() + (ptrdiff_t)i0,
+                                         g.second.begin() +
+                                             (ptrdiff_t)std::min(g.second.size(), i0 + kRegMulti));
+            rf_status s;
+            if (p->opt.order == 3)
+                s = adjoint ? reg_multi_group<3, true>(p, dir, ds, src, out, nvar, st)
+                            : reg_multi_group<3, false>(p, dir, ds, src, out, nvar, st);
+            else
+                s = adjoint ? reg_multi_group<1, true>(p, dir, ds, src, out, nvar, st)
+                            : reg_multi_group<1, false>(p, dir, ds, src, out, nvar, st);
+            RF_TRY(s);
+        }
+    return RF_OK;
+}
+
 // Multi-domain application: x over all domains, then y over all domains
 // (adjoint: y then x); the domains too long for the tile kernel in a
 // direction run on the long-line kernel in the same pass.
@@ -1250,7 +1340,8 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
     // domains no multi-domain launch covers (lines too long for the tile
     // kernel, or no shape fits) launch on their own
     auto covered = [&](const Dir &q, int dir) {
-        if (q.R == 0 || q.rsh.P > 0 || q.kc > 0) return false;   // register-kernel and carried-coast domains launch on their own
+        if (q.rsh.P > 0) return true;   // the multi-domain register launches below
+        if (q.R == 0 || q.kc > 0) return false;   // long-line and carried-coast domains launch on their own
         for (int k = 0; k < nP; ++k)
             if (cs[dir][k].occ > 0 && cs[dir][k].P == q.P) return true;
         return false;
@@ -1272,6 +1363,7 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
         const float *const *src = pass == 0 ? in : (const float *const *)out;
         for (int k = 0; k < nP; ++k)
             if (cs[dir][k].occ > 0) RF_TRY(multi_pass(p, cs[dir][k], src, out, nvar, adjoint, st));
+        RF_TRY(reg_multi_pass(p, dir, src, out, nvar, adjoint, st));
         for (size_t d = 0; d < p->dom.size(); ++d) {
             Domain &D = p->dom[d];
             const Dir &q = D.d[dir];

@@ -457,9 +457,15 @@ constexpr int kRegWaitTries = 1 << 20;
 //   tile together.
 // Both: the CTA's coefficient block arrives by one bulk copy while the data
 // loads are in flight.
-template <int ORDER, bool ADJ, int DIR, int C, int P, int NW, int NPR, bool CARRY = false>
-__global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const RegArgs a)
+// The work of one CTA of one domain's grid (reg_grid): (blockIdx.x,
+// blockIdx.y), or (bx_, by_) in a multi-domain launch (MULTI).
+template <int ORDER, bool ADJ, int DIR, int C, int P, int NW, int NPR, bool CARRY, bool MULTI>
+__device__ __forceinline__ void reg_body(const RegArgs &a, const unsigned bx_, const unsigned by_)
 {
+    // (the single-domain kernel reads the block index where it is used, so
+    // no register holds it across the sweeps)
+#define bx (MULTI ? bx_ : blockIdx.x)
+#define by (MULTI ? by_ : blockIdx.y)
     constexpr int NS = ORDER == 3 ? 3 : 1, MX = RXF<ORDER>::mat;
     static_assert(!CARRY || ORDER == 1, "carried coasts are a first-order option");
     const int RS = CARRY ? a.rs : NS;
@@ -478,10 +484,10 @@ __global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const Re
     const int ql = lane / P, l = lane % P;   // line within the warp, lane on the line
     const int64_t n = a.n;
 
-    const int64_t cline0 = (int64_t)blockIdx.x * LC;                   // first line of the CTA
+    const int64_t cline0 = (int64_t)bx * LC;                   // first line of the CTA
     const int nvalid = (int)min((int64_t)LC, a.nlines - cline0);        // its lines in the grid
     const int64_t line0 = DIR == 0 ? cline0 : cline0 + warp * LPW;      // first line of the warp
-    const int64_t g = DIR == 0 ? (int64_t)blockIdx.y * NW + warp : (int64_t)blockIdx.y;
+    const int64_t g = DIR == 0 ? (int64_t)by * NW + warp : (int64_t)by;
     const bool active = g < a.ngroups;   // x pass: warps past the last group only join barriers
     const int64_t myline0 = line0 + ql;
     const bool line_ok = myline0 < a.nlines;
@@ -748,6 +754,42 @@ __global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const Re
             }
         }
     }
+}
+
+#undef bx
+#undef by
+
+template <int ORDER, bool ADJ, int DIR, int C, int P, int NW, int NPR, bool CARRY = false>
+__global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const RegArgs a)
+{
+    reg_body<ORDER, ADJ, DIR, C, P, NW, NPR, CARRY, false>(a, 0u, 0u);
+}
+
+// One launch over several domains of the same chunking (a ragged batch):
+// the 1-D grid is the concatenation of the domains' grids; cta0[d] is the
+// first CTA of domain d, gx[d] the x extent of its grid.
+constexpr int kRegMulti = 64;
+struct RegMulti {
+    int nd;
+    int gx[kRegMulti];
+    int64_t cta0[kRegMulti + 1];
+    RegArgs dom[kRegMulti];
+};
+
+template <int ORDER, bool ADJ, int DIR, int C, int P, int NW, int NPR, bool CARRY = false>
+__global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4)
+    reg_multi_kernel(const __grid_constant__ RegMulti m)
+{
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = m.nd - 1;   // the domain d with cta0[d] <= b < cta0[d + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (m.cta0[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t r = b - m.cta0[lo];
+    reg_body<ORDER, ADJ, DIR, C, P, NW, NPR, CARRY, true>(m.dom[lo], (unsigned)(r % m.gx[lo]),
+                                                          (unsigned)(r / m.gx[lo]));
 }
 
 }  // namespace rfvh

@@ -44,26 +44,35 @@ def batch():
     return doms, xs
 
 
+def reg_shape(m):
+    """(chunk length, lanes per line) of the register kernel for lines of m
+    points: the first built shape that covers the line."""
+    for C, P in [(16, 8), (16, 16), (24, 16), (16, 32), (24, 32), (32, 32)]:
+        if C * P >= m:
+            return C, P
+
+
 def expected_launches(doms, order):
-    """Kernel launches of one application of the batch: per pass, one for
-    every domain whose lines (at most 1024 points, coefficients shared by
-    all levels) run on the register kernel, one for every domain on the
-    long-line kernel (lines over 4064 points), and one multi-domain launch
-    per lanes-per-line group of the remaining tile-kernel domains (16 lanes
-    for third-order lines of at most 512 points, else 32)."""
+    """Kernel launches of one application of the batch: per pass, one
+    multi-domain register-kernel launch per chunk shape of the domains whose
+    lines (at most 1024 points, coefficients shared by all levels; for the
+    3rd-RF the rows only) run on the register kernel, one for every domain
+    on the long-line kernel (lines over 4064 points), and one multi-domain
+    launch per lanes-per-line group of the remaining tile-kernel domains (16
+    lanes for third-order lines of at most 512 points, else 32)."""
     n = 0
     for along_x in (True, False):
-        groups = set()
+        groups, shapes = set(), set()
         for d in doms:
             shared = np.asarray(d["mask"]).ndim == 2 and np.asarray(d["Lx"]).ndim == 2
             m = d["nx"] if along_x else d["ny"]
-            if shared and m <= 1024:
-                n += 1
+            if shared and m <= 1024 and (along_x or order == 1):
+                shapes.add(reg_shape(m))
             elif m > 4064:
                 n += 1
             else:
                 groups.add(16 if order == 3 and m <= 512 else 32)
-        n += len(groups)
+        n += len(groups) + len(shapes)
     return n
 
 
