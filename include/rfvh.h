@@ -188,16 +188,21 @@ rf_status rf_apply_host(rf_plan p, const float *const *in, float *const *out,
  * synchronisation of cudaMalloc/cudaFree, or real-time loops that may not
  * allocate after start-up.  The paper has no counterpart; it is a service of
  * this library.  It runs the one-thread-per-line kernel for both directions
- * and keeps the per-call scratch (the anticausal start state of every
- * segment end of every slice, 3 floats each) in one static device array of
- * 2^21 floats (8 MiB) inside the library, which every GPU that loads the
- * library holds until the process exits.  The call itself performs no
- * device allocation; the plan (built earlier by rf_coeffs) must exist.
+ * and keeps the per-call scratch (per segment end of every slice the
+ * anticausal start state, r floats: 3; 4 with RF_FLAG_COAST_CONSTANT; 2 + 2K
+ * with RF_FLAG_COAST_CARRIED) in one static device array of 2^21 floats
+ * (8 MiB) inside the library, which every GPU that loads the library holds
+ * until the process exits.  The call itself performs no device allocation;
+ * the plan (built earlier by rf_coeffs) must exist.
  *   in[d], out[d], nvar, stream   as rf_apply
  * Limit: for every domain and direction, nvar * nz * (segment ends of that
- * direction) * 3 must not exceed 2^21, else RF_EINVAL before any launch.
+ * direction) * r must not exceed 2^21, else RF_EINVAL before any launch.
  * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call outside any stream capture.  The kept address does not survive
+ * cudaDeviceReset (or any other teardown of the device's primary context):
+ * after one, the plans are invalid anyway, and this call must not be used
+ * again in the same process.
  * Every call uses the same array: calls that overlap on the GPU (other
  * streams, other threads, other plans) race and give wrong results.  Each
  * call writes every scratch entry it reads, so no clearing is needed.
