@@ -262,8 +262,20 @@ rf_status rf_graph_destroy(rf_graph g);
 rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap);
 
 /* Sticky status of the plan: RF_OK, or the first error a launch or a
- * device-side check recorded since the plan was built. */
+ * device-side check recorded since the plan was built.  RF_ETIMEOUT: a
+ * kernel's bounded wait on an asynchronous copy gave up (the kernel recorded
+ * it, let the copy land and returned without filtering its part; the
+ * context stays usable). */
 rf_status rf_plan_status(rf_plan p);
+
+/* Bound of the kernels' device-side waits for this plan's later launches,
+ * in polls of the waiting mbarrier (each poll may suspend the thread for a
+ * short, system-dependent time).  rf_coeffs sets 2^20, far above any real
+ * copy time; 0 makes every such wait give up at once, which is how the
+ * timeout path (RF_ETIMEOUT from rf_plan_status) is tested without stalling
+ * or faulting a GPU.  The paper has no counterpart.  Errors: RF_EINVAL (null
+ * plan, polls < 0). */
+rf_status rf_plan_set_wait_limit(rf_plan p, int polls);
 
 /* Counts of the plan: total grid points per variable over all domains
  * (nx*ny*nz summed), number of domains, device bytes owned by the plan, and

@@ -76,6 +76,7 @@ def load(build_if_missing: bool = False):
     lib.rf_plan_tune.argtypes = [vp, i, vp]
     lib.rf_plan_tune_batch.argtypes = [vp, i, vp]
     lib.rf_plan_status.argtypes = [vp]
+    lib.rf_plan_set_wait_limit.argtypes = [vp, i]
     lib.rf_plan_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i),
                                  ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.rf_plan_destroy.argtypes = [vp]
@@ -87,7 +88,7 @@ def load(build_if_missing: bool = False):
     lib.rf_status_string.restype = ctypes.c_char_p
     for name in ("rf_options_default", "rf_coeffs", "rf_apply", "rf_apply_adjoint",
                  "rf_apply_host", "rf_apply_static", "rf_plan_tune", "rf_plan_tune_batch",
-                 "rf_plan_status",
+                 "rf_plan_status", "rf_plan_set_wait_limit",
                  "rf_plan_info", "rf_plan_destroy", "rf_plan_describe", "rf_graph_create", "rf_graph_launch",
                  "rf_graph_destroy"):
         getattr(lib, name).restype = i
@@ -160,6 +161,10 @@ def rf_plan_tune_batch(plan, nvar, stream) -> None:
 
 def rf_plan_status(plan) -> int:
     return load().rf_plan_status(plan)
+
+
+def rf_plan_set_wait_limit(plan, polls: int) -> None:
+    check(load().rf_plan_set_wait_limit(plan, int(polls)), "rf_plan_set_wait_limit")
 
 
 def rf_plan_info(plan):

@@ -86,6 +86,7 @@ struct Dir {
 struct Domain {
     rf_grid g{};
     unsigned *status = nullptr;      // the plan's device status word (not owned)
+    const int *wait_polls = nullptr; // the plan's wait bound (not owned)
     int64_t ncl = 1;                 // levels with distinct coefficients
     Dir d[2];                        // 0: x, 1: y
     float *tscr = nullptr;           // boundary-map start states
@@ -119,6 +120,7 @@ struct rf_plan_ {
     rf_status sticky = RF_OK;
     unsigned long long *queue = nullptr;   // work-list counter of multi-domain launches
     unsigned *dstatus = nullptr;           // device status word: bit 0 = a bounded wait gave up
+    int wait_polls = kRegWaitTries;        // bound of the kernels' device-side waits
     cudaStream_t s_in = nullptr, s_out = nullptr;   // copy streams of the host-buffer apply
     cudaEvent_t ev_in = nullptr, ev_done = nullptr, ev_out = nullptr;
     std::vector<MultiCfg> mcfg;            // multi-domain launch shapes chosen so far
@@ -1016,6 +1018,7 @@ RegArgs reg_args(const Domain &D, const Dir &q, const float *in, float *out, int
     a.iters = iters;
     a.zero = 0;
     a.status = D.status;
+    a.wait_polls = D.wait_polls ? *D.wait_polls : kRegWaitTries;
     const bool car = ORDER == 1 && q.kc > 0;
     a.kc = q.kc;
     a.rs = car ? 2 + 2 * q.kc : (ORDER == 3 ? 3 : 1);
@@ -1751,6 +1754,7 @@ rf_status rf_coeffs(const rf_grid *grids, int ndomains, const uint8_t *const *ma
     for (int d = 0; d < ndomains; ++d) {
         P->dom[d].g = grids[d];
         P->dom[d].status = P->dstatus;
+        P->dom[d].wait_polls = &P->wait_polls;
         rf_status s = build_domain(P, P->dom[d], mask[d], Lx[d], Ly[d], st);
         if (s != RF_OK) {
             rf_plan_destroy(P);
@@ -2054,6 +2058,13 @@ rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
     const size_t n = std::min(cap - 1, t.size());
     std::memcpy(buf, t.data(), n);
     buf[n] = '\0';
+    return RF_OK;
+}
+
+rf_status rf_plan_set_wait_limit(rf_plan p, int polls)
+{
+    if (!p || polls < 0) return RF_EINVAL;
+    p->wait_polls = polls;
     return RF_OK;
 }
 

@@ -79,6 +79,7 @@ struct RegArgs {
                               // compiler cannot merge their loads (which would keep every
                               // coefficient of the chunk in registers across the sweeps)
     unsigned *status;         // device status word: bit 0 set if a bounded wait gave up
+    int wait_polls;           // bound of the coefficient copy's wait (polls; 0: give up at once)
     // carried coasts (1st-RF, CARRY kernels): per segment [2][kc - 1] (mu at
     // its end, lambda at its start) of this direction, in boundary-map order
     const float *carry;
@@ -446,7 +447,9 @@ __device__ __forceinline__ void reg_unpack(const u64 (&xp)[C], float *c0, float 
 }
 
 // Bound of the polls of the coefficient copy's mbarrier (each poll may
-// suspend the thread for a while); far above any real copy time.
+// suspend the thread for a while); far above any real copy time.  The
+// plan's wait limit (rf_plan_set_wait_limit) bounds the first wait; after
+// a wait gave up, the drain of the copy in flight uses this bound.
 constexpr int kRegWaitTries = 1 << 20;
 
 // ---------------------------------------------------------------- kernel
@@ -636,7 +639,7 @@ __device__ __forceinline__ void reg_body(const RegArgs &a, const unsigned bx_, c
     }
     // the coefficients must have landed in every thread's view; give up
     // (flag, drain the copy, leave) if they do not arrive
-    if (!__syncthreads_and(mbar_wait(bar, kRegWaitTries))) {
+    if (!__syncthreads_and(mbar_wait(bar, a.wait_polls))) {
         if (threadIdx.x == 0) atomicOr(a.status, 1u);
         mbar_wait(bar, kRegWaitTries);
         return;

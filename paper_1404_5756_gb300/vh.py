@@ -119,6 +119,11 @@ class Plan:
     def status(self) -> int:
         return _lib.rf_plan_status(self._plan)
 
+    def set_wait_limit(self, polls: int) -> None:
+        """Bound of the kernels' device-side waits in polls (0: give up at
+        once, which makes rf_plan_status report RF_ETIMEOUT)."""
+        _lib.rf_plan_set_wait_limit(self._plan, polls)
+
     def close(self):
         if getattr(self, "_plan", None):
             _lib.rf_plan_destroy(self._plan)

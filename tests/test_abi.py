@@ -103,6 +103,7 @@ def test_apply_rejects_bad_arguments(lib):
     assert lib.rf_apply_adjoint(None, arr, arr, 1, None) == E
     assert lib.rf_apply_host(None, arr, arr, 1, 0, None) == E
     assert lib.rf_plan_status(None) == E
+    assert lib.rf_plan_set_wait_limit(None, 0) == E
     assert lib.rf_plan_tune(None, 1, None) == E
     assert lib.rf_plan_info(None, None, None, None, None) == E
     assert lib.rf_plan_destroy(None) == _lib.RF_OK

@@ -4,7 +4,8 @@ whatever sits at land points (NaN, Inf) is ignored and land output is
 exactly 0, and NaN canary bands around every output region are left
 untouched by every kernel path (tile kernel with aligned and unaligned
 rows, both lane widths, long-line kernel, multi-domain launch, in place,
-host-buffer pipeline)."""
+host-buffer pipeline).  A bounded device-side wait that gives up is reported
+as RF_ETIMEOUT and leaves the context usable."""
 import numpy as np
 import pytest
 
@@ -161,3 +162,25 @@ def test_host_pipeline_canaries():
     plan.apply_host(x.pin_memory(), out, nvar=2)
     assert np.isnan(hbuf[:PAD].numpy()).all() and np.isnan(hbuf[-PAD:].numpy()).all()
     assert torch.equal(out, ref)
+
+
+def test_bounded_wait_that_gives_up_reports_timeout():
+    """With a wait bound of 0 polls every register-kernel CTA gives up its
+    wait on the coefficient copy at once: it records the timeout, lets the
+    copy land and returns.  rf_plan_status then reports RF_ETIMEOUT, and the
+    context stays usable: a fresh plan computes the same result as before."""
+    w = synth.workload(2, nz=2, nvar=2)
+    spec = dict(mask=w["mask"], Lx=w["Lx"], Ly=w["Ly"], nz=2)
+    x = torch.from_numpy(w["x"]).cuda()
+    ref = Plan(spec).apply(x)
+    torch.cuda.synchronize()
+    plan = Plan(spec)
+    plan.set_wait_limit(0)
+    plan.apply(x)
+    torch.cuda.synchronize()
+    assert plan.status() == _lib.RF_ETIMEOUT
+    with pytest.raises(_lib.RFError):
+        plan.set_wait_limit(-1)
+    again = Plan(spec).apply(x)
+    torch.cuda.synchronize()
+    assert torch.equal(again, ref)
