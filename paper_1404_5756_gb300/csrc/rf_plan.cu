@@ -19,6 +19,7 @@
 #include "rf_launch.h"
 #include "rf_line.cuh"
 #include "rf_reg_launch.h"
+#include "rf_stream_launch.h"
 #include "rf_tile.cuh"
 
 using namespace rfvh;
@@ -37,6 +38,7 @@ struct TailSpec {
 // How one direction of one domain is launched for a given slice count.
 struct LaunchCfg {
     bool reg = false;      // register-resident kernel (rf_reg.cuh)
+    bool strm = false;     // streaming column kernel (rf_stream.cuh)
     bool tile = false;     // tile kernel (else the long-line kernel, unless reg)
     TileShape sh{0, 0};
     size_t smem = 0;
@@ -80,6 +82,9 @@ struct Dir {
     RegLane *rlanes = nullptr;       // [nlines][P]
     float *rxfer = nullptr;          // [nlines][P][4 * (9 or 1)]
     int max_ends = 0;                // most segment ends on one line
+    // streaming column kernel (third-order y pass, 2-D coefficients): the
+    // coefficients row-major, [n][nlines]
+    float4 *tcoef = nullptr;
     std::vector<CfgEntry> cfgs;      // launch shapes chosen so far
 };
 
@@ -154,6 +159,7 @@ void free_domain(Domain &d)
         cudaFree(q.tail_base);
         cudaFree(q.tmap);
         cudaFree(q.cvec);
+        cudaFree(q.tcoef);
         cudaFree(q.carry);
         cudaFree(q.xfer);
         cudaFree(q.coef_il_base);
@@ -663,6 +669,26 @@ RegShape reg_shape_for(const rf_plan_ *p, const Domain &D, const Dir &q, int dir
     return best;
 }
 
+// Row-major copy of a direction's line-major coefficients, [n][nlines]
+// (for the streaming column kernel).
+__global__ void transpose_coef_kernel(int64_t nlines, int64_t n, const float4 *__restrict__ coef,
+                                      float4 *__restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nlines * n) return;
+    const int64_t r = i / nlines, line = i % nlines;
+    out[i] = coef[line * n + r];
+}
+
+// The streaming column kernel serves the third-order y pass of 2-D
+// coefficients with zero-input coasts whose columns have few enough
+// segment ends for its per-thread records.
+bool stream_ok(const rf_plan_ *p, const Domain &D, const Dir &q, int dir)
+{
+    return p->opt.order == 3 && dir == 1 && D.ncl == 1 && !plan_cst(p) &&
+           q.max_ends <= kStreamMaxEnds;
+}
+
 rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
                     const float *L_dev, const std::vector<int32_t> &base,
                     const std::vector<TailSpec> &sp, int max_re, cudaStream_t st)
@@ -713,6 +739,12 @@ rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,
         RF_TRY(cuda_status(cudaGetLastError()));
     }
     q.rsh = reg_shape_for(P, D, q, dir);
+    if (stream_ok(P, D, q, dir)) {
+        RF_TRY(dev_alloc(&q.tcoef, q.nlines * q.n, &P->bytes));
+        transpose_coef_kernel<<<(unsigned)((q.nlines * q.n + 255) / 256), 256, 0, st>>>(
+            q.nlines, q.n, q.coef, q.tcoef);
+        RF_TRY(cuda_status(cudaGetLastError()));
+    }
     if (q.rsh.P > 0) {
         const int64_t nrec = q.nlines * q.rsh.P;
         RF_TRY(dev_alloc(&q.rcoef, nrec * q.rsh.C, &P->bytes));
@@ -867,6 +899,38 @@ bool reg_cfg(const Dir &q, int64_t nvar, int64_t nk, LaunchCfg &L)
     return L.occ > 0;
 }
 
+// Arguments of the streaming column kernel for one pass of one domain.
+StreamArgs stream_args(const Domain &D, const Dir &q, const float *in, float *out, int64_t nvar,
+                       int64_t k0, int64_t nk)
+{
+    StreamArgs a{};
+    a.in = in;
+    a.out = out;
+    a.coef = q.tcoef;
+    a.tail_base = q.tail_base;
+    a.tmap = q.ntail > 0 ? q.tmap : nullptr;
+    a.n = q.n;
+    a.ncols = q.nlines;
+    a.plane = D.g.nx * D.g.ny;
+    a.nz = D.g.nz;
+    a.k0 = k0;
+    a.nk = nk;
+    a.nslices = nvar * nk;
+    a.npairs = (a.nslices + 1) / 2;
+    return a;
+}
+
+// Configuration of the streaming column kernel, if the direction has it.
+template <int ORDER>
+bool stream_cfg(const Dir &q, LaunchCfg &L)
+{
+    if (ORDER != 3 || !q.tcoef) return false;
+    L = LaunchCfg{};
+    L.strm = true;
+    L.occ = 1;
+    return true;
+}
+
 // Default (untuned) configuration: the register-resident kernel where it
 // applies; else the first tile shape in the direction's preference list
 // whose single-buffered shared memory allows two CTAs per SM, else the
@@ -877,6 +941,7 @@ LaunchCfg launch_cfg(const Domain &D, const Dir &q, int64_t nvar, int64_t nk)
     {
         LaunchCfg L;
         if (reg_cfg<ORDER, ADJ>(q, nvar, nk, L)) return L;
+        if (stream_cfg<ORDER>(q, L)) return L;
     }
     if (q.kc > 0) return LaunchCfg{};   // carried coasts: the long-line kernel
     const int64_t ss = smem_stride(q.n);
@@ -904,7 +969,7 @@ std::vector<LaunchCfg> launch_candidates(const Domain &D, const Dir &q, int64_t 
         // kernel (hence the arithmetic) depends on the line length and the
         // options alone, never on tuning
         LaunchCfg L;
-        if (reg_cfg<ORDER, ADJ>(q, nvar, nk, L)) {
+        if (reg_cfg<ORDER, ADJ>(q, nvar, nk, L) || stream_cfg<ORDER>(q, L)) {
             out.push_back(L);
             return out;
         }
@@ -1041,6 +1106,8 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
             if (q.dir == 0) reg_launch<ORDER, ADJ, 0>(a, q.rsh, L.smem, st);
             else reg_launch<ORDER, ADJ, 1>(a, q.rsh, L.smem, st);
         }
+    } else if (L.strm) {
+        stream_launch<ADJ>(stream_args(D, q, in, out, nvar, k0, nk), st);
     } else if (L.tile) {
         const TileArgs a = tile_args(D, q, in, out, nvar, k0, nk, iters, L.nbuf);
         launch_shape<ORDER, ADJ>(a, L.sh, q.cst, q.nlines, L.groups, L.smem, st);
@@ -1077,7 +1144,7 @@ void launch_dir(const Domain &D, const Dir &q, const LaunchCfg &L, const float *
 // segment-end states in the domain's global scratch).
 bool line_path(const LaunchCfg &L)
 {
-    return !L.tile && !L.reg;
+    return !L.tile && !L.reg && !L.strm;
 }
 
 // Launch configuration of direction dir for nvar variables and batches of
@@ -1150,7 +1217,7 @@ bool multi_fits(const rf_plan_ *p, int dir, int64_t nvar, TileShape sh, size_t *
     bool any = false;
     for (const Domain &D : p->dom) {
         const Dir &q = D.d[dir];
-        if (q.R == 0 || q.P != sh.P || q.rsh.P > 0 || q.kc > 0) continue;   // launched on their own
+        if (q.R == 0 || q.P != sh.P || q.rsh.P > 0 || q.kc > 0 || q.tcoef) continue;   // launched on their own
         m = std::max(m, (size_t)tile_smem_bytes(sh.R, sh.B, smem_stride(q.n), q.max_re, 1,
                                                 rec_floats(q)));
         any = true;
@@ -1212,7 +1279,7 @@ rf_status multi_pass(rf_plan_ *p, const MultiCfg &c, const float *const *src,
     std::vector<int> doms;
     for (size_t d = 0; d < p->dom.size(); ++d)
         if (p->dom[d].d[c.dir].R > 0 && p->dom[d].d[c.dir].P == c.P && p->dom[d].d[c.dir].rsh.P == 0 &&
-            p->dom[d].d[c.dir].kc == 0)
+            p->dom[d].d[c.dir].kc == 0 && !p->dom[d].d[c.dir].tcoef)
             doms.push_back((int)d);
     const int iters = p->opt.order == 3 ? 1 : p->opt.iters;
     const size_t nlaunch = (doms.size() + kMaxMulti - 1) / kMaxMulti;
@@ -1327,6 +1394,39 @@ rf_status reg_multi_pass(rf_plan_ *p, int dir, const float *const *src, float *c
     return RF_OK;
 }
 
+// One pass of the streaming-kernel domains of a batch: one launch over up
+// to kStreamMulti domains, the CTAs of every domain's grid concatenated.
+rf_status stream_multi_pass(rf_plan_ *p, int dir, const float *const *src, float *const *out,
+                            int nvar, bool adjoint, cudaStream_t st)
+{
+    std::vector<size_t> ds;
+    for (size_t d = 0; d < p->dom.size(); ++d)
+        if (p->dom[d].d[dir].tcoef) ds.push_back(d);
+    for (size_t i0 = 0; i0 < ds.size(); i0 += kStreamMulti) {
+        StreamMulti m{};
+        m.nd = (int)std::min<size_t>(kStreamMulti, ds.size() - i0);
+        m.cta0[0] = 0;
+        for (int i = 0; i < m.nd; ++i) {
+            const Domain &D = p->dom[ds[i0 + (size_t)i]];
+            m.dom[i] = stream_args(D, D.d[dir], src[ds[i0 + (size_t)i]], out[ds[i0 + (size_t)i]], nvar, 0,
+                                   D.g.nz);
+            const dim3 g = stream_grid(m.dom[i].ncols, m.dom[i].npairs);
+            m.gx[i] = (int)g.x;
+            m.cta0[i + 1] = m.cta0[i] + (int64_t)g.x * g.y;
+        }
+        if (m.cta0[m.nd] > INT32_MAX) return RF_EINVAL;
+        if (adjoint) stream_launch_multi<true>(m, (unsigned)m.cta0[m.nd], st);
+        else stream_launch_multi<false>(m, (unsigned)m.cta0[m.nd], st);
+        const rf_status s = cuda_status(cudaGetLastError());
+        if (s != RF_OK) {
+            if (p->sticky == RF_OK) p->sticky = s;
+            return s;
+        }
+        ++p->launches;
+    }
+    return RF_OK;
+}
+
 // Multi-domain application: x over all domains, then y over all domains
 // (adjoint: y then x); the domains too long for the tile kernel in a
 // direction run on the long-line kernel in the same pass.
@@ -1343,8 +1443,8 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
     // domains no multi-domain launch covers (lines too long for the tile
     // kernel, or no shape fits) launch on their own
     auto covered = [&](const Dir &q, int dir) {
-        if (q.rsh.P > 0) return true;   // the multi-domain register launches below
-        if (q.R == 0 || q.kc > 0) return false;   // long-line and carried-coast domains launch on their own
+        if (q.rsh.P > 0 || q.tcoef) return true;   // the multi-domain register / streaming launches below
+        if (q.R == 0 || q.kc > 0 || q.tcoef) return false;   // long-line, carried-coast and streaming domains launch on their own
         for (int k = 0; k < nP; ++k)
             if (cs[dir][k].occ > 0 && cs[dir][k].P == q.P) return true;
         return false;
@@ -1367,6 +1467,7 @@ rf_status apply_multi(rf_plan_ *p, const float *const *in, float *const *out, in
         for (int k = 0; k < nP; ++k)
             if (cs[dir][k].occ > 0) RF_TRY(multi_pass(p, cs[dir][k], src, out, nvar, adjoint, st));
         RF_TRY(reg_multi_pass(p, dir, src, out, nvar, adjoint, st));
+        RF_TRY(stream_multi_pass(p, dir, src, out, nvar, adjoint, st));
         for (size_t d = 0; d < p->dom.size(); ++d) {
             Domain &D = p->dom[d];
             const Dir &q = D.d[dir];
@@ -2022,8 +2123,12 @@ rf_status rf_plan_describe(rf_plan p, char *buf, size_t cap)
                               q.rsh.C, q.rsh.P, q.max_ends);
                 t += line;
             }
+            if (q.tcoef) t += "    streaming column kernel\n";
             for (const CfgEntry &e : q.cfgs) {
-                if (e.cfg.reg)
+                if (e.cfg.strm)
+                    std::snprintf(line, sizeof line, "    nvar %lld, %lld levels, %s: streaming kernel\n",
+                                  (long long)e.nvar, (long long)e.nk, e.adjoint ? "adjoint" : "forward");
+                else if (e.cfg.reg)
                     std::snprintf(line, sizeof line,
                                   "    nvar %lld, %lld levels, %s: register kernel C=%d P=%d smem=%zu "
                                   "CTAs/SM=%d\n",

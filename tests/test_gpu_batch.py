@@ -56,23 +56,27 @@ def expected_launches(doms, order):
     """Kernel launches of one application of the batch: per pass, one
     multi-domain register-kernel launch per chunk shape of the domains whose
     lines (at most 1024 points, coefficients shared by all levels; for the
-    3rd-RF the rows only) run on the register kernel, one for every domain
-    on the long-line kernel (lines over 4064 points), and one multi-domain
-    launch per lanes-per-line group of the remaining tile-kernel domains (16
-    lanes for third-order lines of at most 512 points, else 32)."""
+    3rd-RF the rows only) run on the register kernel, one multi-domain launch
+    of the streaming column kernel for the third-order columns of domains
+    with shared coefficients, one for every domain on the long-line kernel
+    (lines over 4064 points), and one multi-domain launch per lanes-per-line
+    group of the remaining tile-kernel domains (16 lanes for third-order
+    lines of at most 512 points, else 32)."""
     n = 0
     for along_x in (True, False):
-        groups, shapes = set(), set()
+        groups, shapes, streams = set(), set(), 0
         for d in doms:
             shared = np.asarray(d["mask"]).ndim == 2 and np.asarray(d["Lx"]).ndim == 2
             m = d["nx"] if along_x else d["ny"]
             if shared and m <= 1024 and (along_x or order == 1):
                 shapes.add(reg_shape(m))
+            elif shared and not along_x and order == 3:
+                streams = 1   # the streaming column kernel, one launch for all
             elif m > 4064:
                 n += 1
             else:
                 groups.add(16 if order == 3 and m <= 512 else 32)
-        n += len(groups) + len(shapes)
+        n += len(groups) + len(shapes) + streams
     return n
 
 
