@@ -1724,6 +1724,9 @@ rf_status host_streams(rf_plan_ *p)
 }
 
 constexpr int64_t kHostBatches = 12;
+// With the streaming column kernel a launch's parallelism is columns x slice
+// pairs, so batches stay larger (fewer, longer launches).
+constexpr int64_t kHostBatchesStream = 4;
 
 // One domain through host buffers, pipelined over batches of levels: the
 // copy in of a batch (stream s_in), its x and y launches (the caller's
@@ -1736,7 +1739,8 @@ rf_status host_pipeline(rf_plan_ *p, Domain &D, const float *in, float *out, int
     const int64_t nz = D.g.nz, plane = D.g.nx * D.g.ny;
     const int64_t n = (int64_t)nvar * nz * plane;
     RF_TRY(ensure(&D.stage, &D.stage_floats, n, &p->bytes));
-    const int64_t nkb = (nz + kHostBatches - 1) / kHostBatches;
+    const int64_t nb = D.d[0].tcoef || D.d[1].tcoef ? kHostBatchesStream : kHostBatches;
+    const int64_t nkb = (nz + nb - 1) / nb;
     int64_t nt = 0;   // scratch of the long-line kernel
     for (int dir = 0; dir < 2; ++dir)
         if (line_path(cfg_of(p, D, dir, nvar, nkb, adjoint)) ||
