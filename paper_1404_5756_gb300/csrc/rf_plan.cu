@@ -682,11 +682,18 @@ __global__ void transpose_coef_kernel(int64_t nlines, int64_t n, const float4 *_
 
 // The streaming column kernel serves the third-order y pass of 2-D
 // coefficients with zero-input coasts whose columns have few enough
-// segment ends for its per-thread records.
+// segment ends for its per-thread records, on domains with at least
+// kStreamMinWork columns x levels: below that its whole-column threads are
+// too few to hide their serial chain of 2 ny steps, and the chunked tile
+// kernel is faster (a 256 x 128 single-level impulse: 25.5 against 39.6 us
+// per application).  A fixed rule per domain, so a domain's results do not
+// depend on the batch it is in.
+constexpr int64_t kStreamMinWork = 16384;
+
 bool stream_ok(const rf_plan_ *p, const Domain &D, const Dir &q, int dir)
 {
     return p->opt.order == 3 && dir == 1 && D.ncl == 1 && !plan_cst(p) &&
-           q.max_ends <= kStreamMaxEnds;
+           q.max_ends <= kStreamMaxEnds && D.g.nx * D.g.nz >= kStreamMinWork;
 }
 
 rf_status build_dir(rf_plan_ *P, Domain &D, int dir, const uint8_t *mask_dev,

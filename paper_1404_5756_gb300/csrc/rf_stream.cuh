@@ -6,11 +6,15 @@
 // coalesced 128-byte row segment.  The first sweep walks the column down,
 // reading the input and the row-major coefficients ([n][ncols] float4,
 // L2-resident) D rows ahead through a register ring, writes its state to the
-// output and keeps the state after each segment end in a per-thread record
-// (local memory, touched only at segment ends).  The coastal maps turn the
-// records into the start states of the second sweep (FP64-built maps applied
-// in compensated FP32).  The second sweep walks back up, reading the first
-// sweep's output, and writes the result.  The x -> y intermediate thus makes
+// output and keeps the state after each segment end in a per-thread record in
+// shared memory.  The coastal maps turn the records into the start states of
+// the second sweep (FP64-built maps applied in compensated FP32).  The second
+// sweep walks back up, reading the first sweep's output, and writes the
+// result.  The record traffic is branch-free: the first sweep stores its
+// state every step (to the next record at a segment end, else to a scratch
+// slot) and the second sweep reloads the next record every step and selects
+// it at a segment end, so the sweeps' code has no data-dependent branches and
+// no segment end waits on a load.  The x -> y intermediate thus makes
 // one extra round trip through memory, in exchange for no chunk re-sweeps,
 // no scans and no barriers.  The forward operator runs the causal sweep
 // first; the adjoint runs the transposed steps in the same order (the
@@ -24,8 +28,12 @@
 
 namespace rfvh {
 
-constexpr int kStreamMaxEnds = 48;   // segment ends per column the records hold
+constexpr int kStreamMaxEnds = 13;   // segment ends per column the records hold
 constexpr int kStreamWarps = 4;      // warps per CTA (slice pairs per CTA)
+constexpr int kStreamThreads = kStreamWarps * 32;
+// records and one scratch slot; 3 u64 per slot and thread, thread-fastest
+// (bank-conflict free): 43 KB per CTA
+constexpr int kStreamSlots = kStreamMaxEnds + 1;
 
 struct StreamArgs {
     const float *in;
@@ -56,14 +64,15 @@ __device__ __forceinline__ float stream_ldf(const float *p)
 
 // One sweep of the column.  DOWN walks rows 0 .. n-1.  FIRST: the sweep
 // reads the input (land zeroed) and records the state after each segment
-// end into rec (counting nr up); else it reads the first sweep's output and
-// injects rec[--nr] before each segment end.  Both write their outputs.
+// end in record nr (counting nr up); else it reads the first sweep's output
+// and injects record --nr before each segment end.  Both write their
+// outputs.  Record e of this thread, component q: sr[(3 e + q) kStreamThreads].
 // Running pointers (one row per step) keep the register count low; the ring
 // holds the next D rows' coefficients and inputs.
 template <bool ADJ, bool DOWN, bool FIRST, int D>
 __device__ __forceinline__ void stream_sweep(const float4 *__restrict__ cp, int64_t ncols,
                                              const float *src0, const float *src1, float *dst0,
-                                             float *dst1, bool ok1, int n, u64 *rec, int &nr)
+                                             float *dst1, bool ok1, int n, u64 *sr, int &nr)
 {
     const int64_t step = DOWN ? ncols : -ncols;
     const int64_t start = DOWN ? 0 : (int64_t)(n - 1) * ncols;
@@ -71,6 +80,12 @@ __device__ __forceinline__ void stream_sweep(const float4 *__restrict__ cp, int6
     const float *p0 = src0 + start, *p1 = src1 + start;
     float *w0 = dst0 + start, *w1 = dst1 + start;
     u64 st[3] = {0ull, 0ull, 0ull};
+    u64 nx[3] = {0ull, 0ull, 0ull};
+    if (!FIRST) {
+        const int e = nr > 0 ? nr - 1 : 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) nx[q] = sr[(3 * e + q) * kStreamThreads];
+    }
     const u64 one = V2::bc(1.f);
     float4 rc[D];
     float r0[D], r1[D];
@@ -103,10 +118,13 @@ __device__ __forceinline__ void stream_sweep(const float4 *__restrict__ cp, int6
             const bool end = __float_as_uint(c.x) >> 31;
             c.x = fabsf(c.x);
             const bool sea = c.x != 0.f;
-            if (!FIRST && end) {
-                --nr;
+            if (!FIRST) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) st[q] = rec[3 * nr + q];
+                for (int q = 0; q < 3; ++q) st[q] = end ? nx[q] : st[q];
+                nr -= end;
+                const int e = nr > 0 ? nr - 1 : 0;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) nx[q] = sr[(3 * e + q) * kStreamThreads];
             }
             const u64 g = sea ? one : 0ull;
             const u64 x = FIRST ? V2::pack(sea ? u : 0.f, sea ? w : 0.f) : V2::pack(u, w);
@@ -116,10 +134,12 @@ __device__ __forceinline__ void stream_sweep(const float4 *__restrict__ cp, int6
             if (ok1) *w1 = V2::get(y, 1);
             w0 += step;
             w1 += step;
-            if (FIRST && end && nr < kStreamMaxEnds) {
+            if (FIRST) {
+                const bool keep = end && nr < kStreamMaxEnds;
+                const int e = keep ? nr : kStreamMaxEnds;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) rec[3 * nr + q] = st[q];
-                ++nr;
+                for (int q = 0; q < 3; ++q) sr[(3 * e + q) * kStreamThreads] = st[q];
+                nr += keep;
             }
         }
     }
@@ -137,38 +157,43 @@ __device__ __forceinline__ void stream_body(const StreamArgs &a, unsigned bx, un
     const int64_t o0 = ((s0 / a.nk) * a.nz + a.k0 + s0 % a.nk) * a.plane;
     const int64_t o1 = ok1 ? ((s1 / a.nk) * a.nz + a.k0 + s1 % a.nk) * a.plane : o0;
     const float4 *cp = a.coef + col;
-    u64 rec[3 * kStreamMaxEnds];
+    __shared__ u64 srec[3 * kStreamSlots * kStreamThreads];
+    u64 *sr = srec + threadIdx.x;
     int nr = 0;
     // first sweep: down, recording the states at the segment ends
     stream_sweep<ADJ, true, true, D>(cp, a.ncols, a.in + o0 + col, a.in + o1 + col, a.out + o0 + col,
-                                     a.out + o1 + col, ok1, (int)a.n, rec, nr);
+                                     a.out + o1 + col, ok1, (int)a.n, sr, nr);
     // the coastal maps of the column's ends, in order (zero start states
     // without imaginary points)
     const float2 *ml = a.tmap ? a.tmap + 9 * (int64_t)a.tail_base[col] : nullptr;
     for (int q = 0; q < nr; ++q) {
-        u64 *r = rec + 3 * q;
+        u64 r[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] = sr[(3 * q + k) * kStreamThreads];
         if (!ml) {
             r[0] = r[1] = r[2] = 0ull;
-            continue;
-        }
+        } else {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float X[3], Y[3];
+            for (int h = 0; h < 2; ++h) {
+                float X[3], Y[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) X[k] = V2::get(r[k], h);
-            apply_tail<3, ADJ>(ml + 9 * q, X, Y);
+                for (int k = 0; k < 3; ++k) X[k] = V2::get(r[k], h);
+                apply_tail<3, ADJ>(ml + 9 * q, X, Y);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float lo = V2::get(r[k], 0), hi = V2::get(r[k], 1);
-                if (h == 0) lo = Y[k];
-                else hi = Y[k];
-                r[k] = V2::pack(lo, hi);
+                for (int k = 0; k < 3; ++k) {
+                    float lo = V2::get(r[k], 0), hi = V2::get(r[k], 1);
+                    if (h == 0) lo = Y[k];
+                    else hi = Y[k];
+                    r[k] = V2::pack(lo, hi);
+                }
             }
         }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sr[(3 * q + k) * kStreamThreads] = r[k];
     }
     // second sweep: up, from the first sweep's output in place
     stream_sweep<ADJ, false, false, D>(cp, a.ncols, a.out + o0 + col, a.out + o1 + col, a.out + o0 + col,
-                                       a.out + o1 + col, ok1, (int)a.n, rec, nr);
+                                       a.out + o1 + col, ok1, (int)a.n, sr, nr);
 }
 
 template <bool ADJ, int D>

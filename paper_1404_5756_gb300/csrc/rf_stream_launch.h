@@ -9,7 +9,7 @@
 
 namespace rfvh {
 
-constexpr int kStreamDepth = 12;  // rows read ahead
+constexpr int kStreamDepth = 10;  // rows read ahead
 
 // Grid of a pass: (column blocks of 32, slice-pair blocks of kStreamWarps).
 inline dim3 stream_grid(int64_t ncols, int64_t npairs)

@@ -52,16 +52,28 @@ def reg_shape(m):
             return C, P
 
 
+STREAM_MAX_ENDS = 13   # segment ends per column the streaming kernel's records hold
+STREAM_MIN_WORK = 16384   # columns x levels of a domain below which the tile kernel serves
+
+
+def column_ends(mask):
+    """Most segment ends (a sea point followed by land or the edge) on one
+    column of a 2-D mask."""
+    m = np.asarray(mask).astype(bool)
+    return int((m & ~np.vstack([m[1:], np.zeros((1, m.shape[1]), bool)])).sum(0).max())
+
+
 def expected_launches(doms, order):
     """Kernel launches of one application of the batch: per pass, one
     multi-domain register-kernel launch per chunk shape of the domains whose
     lines (at most 1024 points, coefficients shared by all levels; for the
     3rd-RF the rows only) run on the register kernel, one multi-domain launch
     of the streaming column kernel for the third-order columns of domains
-    with shared coefficients, one for every domain on the long-line kernel
-    (lines over 4064 points), and one multi-domain launch per lanes-per-line
-    group of the remaining tile-kernel domains (16 lanes for third-order
-    lines of at most 512 points, else 32)."""
+    with shared coefficients, at most STREAM_MAX_ENDS segment ends per
+    column and at least STREAM_MIN_WORK columns x levels, one for every domain on the long-line kernel (lines over 4064
+    points), and one multi-domain launch per lanes-per-line group of the
+    remaining tile-kernel domains (16 lanes for third-order lines of at most
+    512 points, else 32)."""
     n = 0
     for along_x in (True, False):
         groups, shapes, streams = set(), set(), 0
@@ -70,7 +82,9 @@ def expected_launches(doms, order):
             m = d["nx"] if along_x else d["ny"]
             if shared and m <= 1024 and (along_x or order == 1):
                 shapes.add(reg_shape(m))
-            elif shared and not along_x and order == 3:
+            elif (shared and not along_x and order == 3
+                  and column_ends(d["mask"]) <= STREAM_MAX_ENDS
+                  and d["nx"] * d["nz"] >= STREAM_MIN_WORK):
                 streams = 1   # the streaming column kernel, one launch for all
             elif m > 4064:
                 n += 1
