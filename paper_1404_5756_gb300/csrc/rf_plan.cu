@@ -663,7 +663,7 @@ RegShape reg_shape_for(const rf_plan_ *p, const Domain &D, const Dir &q, int dir
             break;
         }
     if (best.P == 0) return best;
-    if (reg_smem_bytes(dir, p->opt.order, best.C, best.P, kRegWarps, q.max_ends, kRegPairs,
+    if (reg_smem_bytes(dir, p->opt.order, best.C, best.P, kRegWarps, q.max_ends, reg_pairs(p->opt.order),
                        plan_carry(p) ? 2 + 2 * p->opt.iters : 0) > (int64_t)kSmemMax)
         return RegShape{0, 0};
     return best;
@@ -890,13 +890,13 @@ template <int ORDER, bool ADJ>
 bool reg_cfg(const Dir &q, int64_t nvar, int64_t nk, LaunchCfg &L)
 {
     if (q.rsh.P == 0) return false;
-    const int64_t ngroups = (nvar * nk + 2 * kRegPairs - 1) / (2 * kRegPairs);
+    const int64_t ngroups = (nvar * nk + 2 * reg_pairs(ORDER) - 1) / (2 * reg_pairs(ORDER));
     if ((q.dir == 0 ? (ngroups + kRegWarps - 1) / kRegWarps : ngroups) > 65535) return false;
     L = LaunchCfg{};
     L.reg = true;
     const bool car = ORDER == 1 && q.kc > 0;
     L.smem = (size_t)reg_smem_bytes(q.dir, ORDER, q.rsh.C, q.rsh.P, kRegWarps, q.max_ends,
-                                    kRegPairs, car ? 2 + 2 * q.kc : 0);
+                                    reg_pairs(ORDER), car ? 2 + 2 * q.kc : 0);
     if (car)
         L.occ = q.dir == 0 ? reg_occupancy<1, ADJ, 0, true>(q.rsh, L.smem)
                            : reg_occupancy<1, ADJ, 1, true>(q.rsh, L.smem);
@@ -924,6 +924,7 @@ StreamArgs stream_args(const Domain &D, const Dir &q, const float *in, float *ou
     a.nk = nk;
     a.nslices = nvar * nk;
     a.npairs = (a.nslices + 1) / 2;
+    a.scratch = q.max_ends;
     return a;
 }
 
@@ -1084,7 +1085,7 @@ RegArgs reg_args(const Domain &D, const Dir &q, const float *in, float *out, int
     a.k0 = k0;
     a.nk = nk;
     a.nslices = nvar * nk;
-    a.ngroups = (a.nslices + 2 * kRegPairs - 1) / (2 * kRegPairs);
+    a.ngroups = (a.nslices + 2 * reg_pairs(ORDER) - 1) / (2 * reg_pairs(ORDER));
     a.max_re = q.max_ends;
     a.vec4 = D.g.nx % 4 == 0 && ((uintptr_t)in % 16) == 0 && ((uintptr_t)out % 16) == 0;
     a.iters = iters;
@@ -1348,7 +1349,7 @@ rf_status reg_multi_group(rf_plan_ *p, int dir, const std::vector<size_t> &ds,
         m.gx[i] = (int)g.x;
         m.cta0[i + 1] = m.cta0[i] + (int64_t)g.x * g.y;
         smem = std::max(smem, (size_t)reg_smem_bytes(dir, ORDER, sh.C, sh.P, kRegWarps, q.max_ends,
-                                                     kRegPairs, car ? 2 + 2 * q.kc : 0));
+                                                     reg_pairs(ORDER), car ? 2 + 2 * q.kc : 0));
     }
     if (m.cta0[m.nd] > INT32_MAX) return RF_EINVAL;
     const unsigned grid = (unsigned)m.cta0[m.nd];

@@ -763,7 +763,7 @@ __device__ __forceinline__ void reg_body(const RegArgs &a, const unsigned bx_, c
 #undef by
 
 template <int ORDER, bool ADJ, int DIR, int C, int P, int NW, int NPR, bool CARRY = false>
-__global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4) reg_kernel(const RegArgs a)
+__global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 3) reg_kernel(const RegArgs a)
 {
     reg_body<ORDER, ADJ, DIR, C, P, NW, NPR, CARRY, false>(a, 0u, 0u);
 }
@@ -780,7 +780,7 @@ struct RegMulti {
 };
 
 template <int ORDER, bool ADJ, int DIR, int C, int P, int NW, int NPR, bool CARRY = false>
-__global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 4)
+__global__ void __launch_bounds__(NW * 32, NPR == 2 ? 2 : 3)
     reg_multi_kernel(const __grid_constant__ RegMulti m)
 {
     const int64_t b = blockIdx.x;

@@ -23,10 +23,10 @@ void reg_smem_attr(size_t smem)
     std::lock_guard<std::mutex> lock(mu);
     if (dev >= 0 && dev < kRegAttrDevices && smem <= done[dev]) return;
     if (MULTI)
-        cudaFuncSetAttribute(reg_multi_kernel<ORDER, ADJ, DIR, C, P, kRegWarps, kRegPairs, CARRY>,
+        cudaFuncSetAttribute(reg_multi_kernel<ORDER, ADJ, DIR, C, P, kRegWarps, reg_pairs(ORDER), CARRY>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else
-        cudaFuncSetAttribute(reg_kernel<ORDER, ADJ, DIR, C, P, kRegWarps, kRegPairs, CARRY>,
+        cudaFuncSetAttribute(reg_kernel<ORDER, ADJ, DIR, C, P, kRegWarps, reg_pairs(ORDER), CARRY>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < kRegAttrDevices) done[dev] = smem;
 }
@@ -41,7 +41,7 @@ bool reg_launch(const RegArgs &a, RegShape sh, size_t smem, cudaStream_t st)
 #define RF_REG_SHAPE(c, p)                                                                \
     if (sh.C == c && sh.P == p) {                                                         \
         reg_smem_attr<ORDER, ADJ, DIR, c, p, CARRY>(smem);                                \
-        reg_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, kRegPairs, CARRY>                    \
+        reg_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, reg_pairs(ORDER), CARRY>                    \
             <<<reg_grid(DIR, sh, a.nlines, a.ngroups), kRegWarps * 32, smem, st>>>(a);    \
         return true;                                                                      \
     }
@@ -56,7 +56,7 @@ bool reg_launch_multi(const RegMulti &m, RegShape sh, size_t smem, unsigned grid
 #define RF_REG_SHAPE(c, p)                                                                \
     if (sh.C == c && sh.P == p) {                                                         \
         reg_smem_attr<ORDER, ADJ, DIR, c, p, CARRY, true>(smem);                          \
-        reg_multi_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, kRegPairs, CARRY>              \
+        reg_multi_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, reg_pairs(ORDER), CARRY>              \
             <<<grid, kRegWarps * 32, smem, st>>>(m);                                      \
         return true;                                                                      \
     }
@@ -73,7 +73,7 @@ int reg_occupancy(RegShape sh, size_t smem)
         reg_smem_attr<ORDER, ADJ, DIR, c, p, CARRY>(smem);                                 \
         int blocks = 0;                                                                    \
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                 \
-                &blocks, reg_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, kRegPairs, CARRY>,   \
+                &blocks, reg_kernel<ORDER, ADJ, DIR, c, p, kRegWarps, reg_pairs(ORDER), CARRY>,   \
                 kRegWarps * 32, smem)                                                      \
             != cudaSuccess) {                                                              \
             cudaGetLastError();                                                            \

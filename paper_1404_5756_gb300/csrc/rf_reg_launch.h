@@ -14,7 +14,10 @@
 namespace rfvh {
 
 constexpr int kRegWarps = 4;   // warps per CTA
-constexpr int kRegPairs = 2;   // slice pairs per thread (4 slices)
+// Slice pairs per thread: one for the third-order filter (168 registers at
+// 32-point chunks, three CTAs and twelve warps per SM), two for the first
+// order (its two-term steps leave room for four slices at two CTAs per SM).
+constexpr int reg_pairs(int order) { return order == 3 ? 1 : 2; }
 
 struct RegShape {
     int C, P;   // chunk length, lanes per line

@@ -31,9 +31,16 @@ namespace rfvh {
 constexpr int kStreamMaxEnds = 13;   // segment ends per column the records hold
 constexpr int kStreamWarps = 4;      // warps per CTA (slice pairs per CTA)
 constexpr int kStreamThreads = kStreamWarps * 32;
-// records and one scratch slot; 3 u64 per slot and thread, thread-fastest
-// (bank-conflict free): 43 KB per CTA
-constexpr int kStreamSlots = kStreamMaxEnds + 1;
+
+// Dynamic shared memory of a launch whose domains have at most `ends`
+// segment ends per column: that many records and one scratch slot, 3 u64
+// per slot and thread, thread-fastest (bank-conflict free); at most 43 KB
+// per CTA.  Sizing it to the domains' own ends leaves the rest of the SM's
+// memory to L1, which keeps the coefficient rows the CTAs share.
+inline size_t stream_smem_bytes(int ends)
+{
+    return (size_t)3 * (ends + 1) * kStreamThreads * sizeof(uint64_t);
+}
 
 struct StreamArgs {
     const float *in;
@@ -45,6 +52,7 @@ struct StreamArgs {
     int64_t plane;            // floats per slice
     int64_t nz, k0, nk;       // slices of this launch: (s / nk) * nz + k0 + s % nk
     int64_t nslices, npairs;  // slices, ceil(nslices / 2)
+    int scratch;              // scratch record slot = most segment ends per column (<= kStreamMaxEnds)
 };
 
 __device__ __forceinline__ float4 stream_ldc(const float4 *p)
@@ -72,7 +80,8 @@ __device__ __forceinline__ float stream_ldf(const float *p)
 template <bool ADJ, bool DOWN, bool FIRST, int D>
 __device__ __forceinline__ void stream_sweep(const float4 *__restrict__ cp, int64_t ncols,
                                              const float *src0, const float *src1, float *dst0,
-                                             float *dst1, bool ok1, int n, u64 *sr, int &nr)
+                                             float *dst1, bool ok1, int n, u64 *sr, int scratch,
+                                             int &nr)
 {
     const int64_t step = DOWN ? ncols : -ncols;
     const int64_t start = DOWN ? 0 : (int64_t)(n - 1) * ncols;
@@ -135,8 +144,8 @@ __device__ __forceinline__ void stream_sweep(const float4 *__restrict__ cp, int6
             w0 += step;
             w1 += step;
             if (FIRST) {
-                const bool keep = end && nr < kStreamMaxEnds;
-                const int e = keep ? nr : kStreamMaxEnds;
+                const bool keep = end && nr < scratch;
+                const int e = keep ? nr : scratch;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) sr[(3 * e + q) * kStreamThreads] = st[q];
                 nr += keep;
@@ -157,12 +166,12 @@ __device__ __forceinline__ void stream_body(const StreamArgs &a, unsigned bx, un
     const int64_t o0 = ((s0 / a.nk) * a.nz + a.k0 + s0 % a.nk) * a.plane;
     const int64_t o1 = ok1 ? ((s1 / a.nk) * a.nz + a.k0 + s1 % a.nk) * a.plane : o0;
     const float4 *cp = a.coef + col;
-    __shared__ u64 srec[3 * kStreamSlots * kStreamThreads];
-    u64 *sr = srec + threadIdx.x;
+    extern __shared__ u64 stream_srec[];   // stream_smem_bytes(scratch of the launch's domains)
+    u64 *sr = stream_srec + threadIdx.x;
     int nr = 0;
     // first sweep: down, recording the states at the segment ends
     stream_sweep<ADJ, true, true, D>(cp, a.ncols, a.in + o0 + col, a.in + o1 + col, a.out + o0 + col,
-                                     a.out + o1 + col, ok1, (int)a.n, sr, nr);
+                                     a.out + o1 + col, ok1, (int)a.n, sr, a.scratch, nr);
     // the coastal maps of the column's ends, in order (zero start states
     // without imaginary points)
     const float2 *ml = a.tmap ? a.tmap + 9 * (int64_t)a.tail_base[col] : nullptr;
@@ -193,7 +202,7 @@ __device__ __forceinline__ void stream_body(const StreamArgs &a, unsigned bx, un
     }
     // second sweep: up, from the first sweep's output in place
     stream_sweep<ADJ, false, false, D>(cp, a.ncols, a.out + o0 + col, a.out + o1 + col, a.out + o0 + col,
-                                       a.out + o1 + col, ok1, (int)a.n, sr, nr);
+                                       a.out + o1 + col, ok1, (int)a.n, sr, a.scratch, nr);
 }
 
 template <bool ADJ, int D>
