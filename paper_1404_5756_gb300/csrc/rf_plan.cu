@@ -1733,8 +1733,11 @@ rf_status host_streams(rf_plan_ *p)
 
 constexpr int64_t kHostBatches = 12;
 // With the streaming column kernel a launch's parallelism is columns x slice
-// pairs, so batches stay larger (fewer, longer launches).
-constexpr int64_t kHostBatchesStream = 4;
+// pairs and its serial chain of 2 ny steps sets a floor under each launch, so
+// batches stay larger: on the regional workload 8 batches ran end to end at
+// 34.1 Gpts/s against 32.0 with 4 and 17.8 with 12, whose launches outlast
+// their copies.
+constexpr int64_t kHostBatchesStream = 8;
 
 // One domain through host buffers, pipelined over batches of levels: the
 // copy in of a batch (stream s_in), its x and y launches (the caller's
