@@ -14,9 +14,9 @@
 // state every step (to the next record at a segment end, else to a scratch
 // slot) and the second sweep reloads the next record every step and selects
 // it at a segment end, so the sweeps' code has no data-dependent branches and
-// no segment end waits on a load.  The x -> y intermediate thus makes
-// one extra round trip through memory, in exchange for no chunk re-sweeps,
-// no scans and no barriers.  The forward operator runs the causal sweep
+// no segment end waits on a load.  The first sweep's output thus makes one
+// round trip through memory between the sweeps, in exchange for no chunk
+// re-sweeps, no scans and no barriers.  The forward operator runs the causal sweep
 // first; the adjoint runs the transposed steps in the same order (the
 // transposed anticausal sweep first, walking down) with the transposed maps.
 // Land carries (0, 0, 0, -1) with the reset factor g = 0; the sign of beta
